@@ -1,0 +1,407 @@
+"""Benchmark: the Pregel superstep hot path on the billion-edge workload.
+
+One step = PageRank (10 supersteps, FP32, pull) + SSSP from the max-out-degree vertex
+(u32 weights in [1,255], push with a min combiner) on a directed R-MAT graph of scale
+26 and edge factor 28 (1.84e9 edges after self-loop and duplicate removal, seed 1),
+synthetic input standing in for the paper's billion-edge Friendster graph.
+
+value      edges traversed per second (PageRank: 10 m; SSSP: messages sent), graph
+           resident in HBM, timed with CUDA events on the library's stream.
+e2e        the same metric through the host-buffer C ABI: ipg_graph_create from pinned
+           host CSR (upload + in-edge build), ipg_pagerank and ipg_sssp into host
+           arrays, ipg_graph_destroy, every step.
+roofline   the dominant kernel's algorithmic bytes per launch / its mean CUDA-event
+           duration, against the measured HBM copy bandwidth.
+cpu_baseline  the CPU oracle (single thread) on a bounded sample of the same graph.
+
+Multi-GPU: the path does not shard here; with --gpus N every rank runs its own replica
+(scaling "weak"), value = all ranks' edges / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GTEPS (edges traversed per second: PageRank 10 supersteps + SSSP), per superstep roofline"
+UNIT = "GTEPS"
+PR_UPDATES = 10
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--scale", type=int, default=26)
+    p.add_argument("--edge-factor", type=int, default=28)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_name(a):
+    return (f"rmat{a.scale}-ef{a.edge_factor} directed weighted[1,255] seed {a.seed}: "
+            f"PageRank {PR_UPDATES} supersteps + SSSP from the max-out-degree vertex")
+
+
+# ---------------------------------------------------------------------------------------
+# distributed plumbing
+
+
+def dist_init(a):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        dist.barrier()
+        torch.cuda.synchronize()
+
+
+def all_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------
+# clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------
+# oracle sample (CPU baseline and the reference arm)
+
+
+def prefix_subgraph(g, edges):
+    """The first source rows of g holding about `edges` edges, over all n vertices."""
+    S = int(np.searchsorted(g.offsets, edges, side="right")) - 1
+    S = max(1, min(S, g.n))
+    mS = int(g.offsets[S])
+    off = g.offsets.copy()
+    off[S + 1:] = mS
+    return S, mS, off, g.cols[:mS], None if g.weights is None else g.weights[:mS]
+
+
+def oracle_sample(g, src, edges):
+    """Oracle PageRank (one update) + SSSP on the row-prefix subgraph; returns (edges traversed, seconds)."""
+    import oracle
+
+    S, mS, off, cols, w = prefix_subgraph(g, edges)
+    t0 = time.perf_counter()
+    pr = oracle.pagerank(g.n, off, cols, 1)
+    ss = oracle.sssp(g.n, off, cols, w, src if src < S else 0)
+    t = time.perf_counter() - t0
+    traversed = sum(s.messages_sent for s in pr.stats) + sum(s.messages_sent for s in ss.stats)
+    return traversed, t, S, mS
+
+
+def calibrate_sample(g, src, seconds):
+    edges = 20_000_000
+    tr, t, _, _ = oracle_sample(g, src, edges)
+    rate = tr / max(t, 1e-6)  # edges traversed per second
+    per_edge = tr / max(edges, 1)
+    return int(min(g.m, max(1_000_000, seconds * rate / max(per_edge, 1e-9))))
+
+
+def cpu_baseline(g, src, seconds):
+    edges = calibrate_sample(g, src, seconds)
+    tr, t, S, mS = oracle_sample(g, src, edges)
+    return {"value": tr / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle PageRank (1 update) + SSSP to quiescence on the first {S} source rows "
+                      f"({mS} edges) of the same graph, all n vertices; {tr} edges traversed in {t:.1f} s"}
+
+
+# ---------------------------------------------------------------------------------------
+# roofline helpers
+
+
+def kernel_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+PR_KERNEL_FILES = ["paper_2010_01542_gb300/csrc/ipg_pagerank.cu", "paper_2010_01542_gb300/csrc/ipg_internal.cuh"]
+
+
+def measured_traffic(kernel, n, m):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))[kernel]
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_hash(PR_KERNEL_FILES):
+        return None
+    # captured on a smaller graph of the same family: scale by algorithmic units
+    units = 8 * m + 24 * n
+    return d["dram_bytes_per_launch"] * units / d["algorithmic_bytes_per_launch"]
+
+
+def peak_hbm():
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------
+
+
+def run_ours(a):
+    import torch
+
+    import gen
+    import paper_2010_01542_gb300 as ipg
+
+    world, rank, local = dist_init(a)
+    ipg.load_library()
+    dg = gen.rmat_device(a.scale, a.edge_factor, seed=a.seed, weighted=True, device=local)
+    n, m = dg.n, dg.m
+    stream = torch.cuda.Stream()
+    h = ipg.ipg_graph_create_dev(dg.offsets, dg.cols, dg.weights, n, m, True, stream=stream)
+    host = dg.to_host(pinned=True)
+    del dg
+    torch.cuda.empty_cache()
+    src = gen.max_out_degree_vertex(host)
+    ranks = torch.empty(n, dtype=torch.float32, device="cuda")
+    dist = torch.empty(n, dtype=torch.int32, device="cuda")
+    flags = ipg.IPG_STAT_TIMING
+
+    def step():
+        c1, pst = ipg.ipg_pagerank_dev(h, PR_UPDATES, ranks, stats_flags=flags, stream=stream)
+        c2, sst = ipg.ipg_sssp_dev(h, src, dist, stats_flags=flags, stream=stream)
+        return pst, sst
+
+    for _ in range(max(a.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    all_stats = [step() for _ in range(a.steps)]
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = t_start.elapsed_time(t_end)
+    ms_max = all_max(ms, world)
+
+    pr_edges = PR_UPDATES * m
+    sssp_edges = [sum(s.messages_sent for s in sst) for _, sst in all_stats]
+    edges_per_step = pr_edges + statistics.mean(sssp_edges)
+    value = world * edges_per_step * a.steps / (ms_max / 1e3) / 1e9
+    pr_kernel_ms = [s.kernel_ms for pst, _ in all_stats for s in pst[:PR_UPDATES]]
+    pr_step_ms = [s.superstep_ms for pst, _ in all_stats for s in pst[:PR_UPDATES]]
+    sssp_kernel_ms = [sum(s.kernel_ms for s in sst) for _, sst in all_stats]
+    sssp_ms = [sum(s.superstep_ms for s in sst) for _, sst in all_stats]
+    sssp_supersteps = [len(sst) for _, sst in all_stats]
+    launches_per_step = (1 + 2 * PR_UPDATES) + statistics.mean(
+        1 + 5 * sum(1 for s in sst if s.senders > 0) for _, sst in all_stats)
+
+    # roofline: the PageRank pull kernel (the dominant kernel of the step)
+    alg_bytes = 8 * m + 24 * n
+    pr_mean = statistics.mean(pr_kernel_ms)
+    achieved = alg_bytes / (pr_mean / 1e3) / 1e9
+    peak, peak_kind = peak_hbm()
+    traffic = measured_traffic("pr_pull_kernel", n, m)
+    roofline = {"bound": "hbm", "kernel": "pr_pull_kernel", "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None if traffic is None else int(traffic),
+                "algorithmic_bytes": alg_bytes, "kernel_ms": round(pr_mean, 4)}
+
+    # end to end through the host-buffer C ABI
+    e2e = None
+    if a.e2e_steps > 0:
+        out_r = np.empty(n, dtype=np.float32)
+        out_d = np.empty(n, dtype=np.uint32)
+        try:
+            out_r = torch.empty(n, dtype=torch.float32, pin_memory=True).numpy()
+            out_d = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+        except Exception:
+            pass
+        times, e2e_edges = [], []
+        for i in range(a.e2e_steps + 1):  # the first round is a warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2 = ipg.ipg_graph_create(host.offsets, host.cols, host.weights, n, m, True)
+            _, c1, _ = ipg.ipg_pagerank(g2, PR_UPDATES, out_r)
+            _, c2, sst = ipg.ipg_sssp(g2, src, out_d, stats_flags=0)
+            ipg.ipg_graph_destroy(g2)
+            dt = time.perf_counter() - t0
+            if i > 0:
+                times.append(dt)
+                e2e_edges.append(pr_edges + statistics.mean(sssp_edges))
+        t_e2e = all_max(statistics.mean(times), world)
+        e2e = {"value": round(world * statistics.mean(e2e_edges) / t_e2e / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(host.offsets.nbytes + host.cols.nbytes + host.weights.nbytes),
+               "d2h_bytes_per_step": int(out_r.nbytes + out_d.nbytes), "ms_per_step": round(t_e2e * 1e3, 2),
+               "api": "ipg_graph_create + ipg_pagerank + ipg_sssp + ipg_graph_destroy, host buffers"}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        cpu = cpu_baseline(host, src, a.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms_max / a.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+u32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "scale": a.scale, "edge_factor": a.edge_factor, "n": n, "m": m,
+                       "sssp_source": src, "l2": "inputs larger than L2 (graph %.1f GB resident)" %
+                       ((host.offsets.nbytes + 2 * host.cols.nbytes) / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(round(launches_per_step * a.steps)), "clocks": clocks,
+            "pagerank": {"edges_per_step": pr_edges, "ms_per_superstep": round(statistics.mean(pr_step_ms), 4),
+                         "kernel_ms": round(pr_mean, 4),
+                         "gteps": round(m / (statistics.mean(pr_step_ms) / 1e3) / 1e9, 2)},
+            "sssp": {"edges_per_step": int(statistics.mean(sssp_edges)), "supersteps": sssp_supersteps[0],
+                     "ms": round(statistics.mean(sssp_ms), 3), "kernel_ms": round(statistics.mean(sssp_kernel_ms), 3),
+                     "gteps": round(statistics.mean(sssp_edges) / (statistics.mean(sssp_ms) / 1e3) / 1e9, 2)},
+        }
+        print(json.dumps(line), flush=True)
+    h.destroy()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_reference(a):
+    """The oracle, as it stands, on the host cores: each step is a bounded sample of the
+    same workload (row-prefix subgraph, PageRank one update + SSSP)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import gen
+
+    import torch
+
+    if torch.cuda.is_available():
+        g = gen.rmat_device(a.scale, a.edge_factor, seed=a.seed, weighted=True).to_host()
+    else:
+        g = gen.rmat(a.scale, a.edge_factor, seed=a.seed, weighted=True)
+    src = gen.max_out_degree_vertex(g)
+    budget = 150.0 / max(1, a.steps + a.warmup)
+    edges = calibrate_sample(g, src, budget)
+    for _ in range(a.warmup):
+        oracle_sample(g, src, edges)
+    trav, secs = 0, 0.0
+    desc = None
+    for _ in range(a.steps):
+        tr, t, S, mS = oracle_sample(g, src, edges)
+        trav += tr
+        secs += t
+        desc = (f"oracle PageRank (1 update) + SSSP to quiescence on the first {S} source rows ({mS} edges) "
+                f"of the same graph, all n vertices, 1 thread")
+    value = trav / secs / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(secs / a.steps * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+u32",
+            "data": "synthetic", "config": {"workload": workload_name(a), "scale": a.scale,
+                                            "edge_factor": a.edge_factor, "n": g.n, "m": g.m},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

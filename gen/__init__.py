@@ -191,3 +191,98 @@ def random_multigraph(n: int, m: int, seed: int, undirected: bool = False, weigh
         src = src[:dst.size]
     w = rng.integers(1, wmax + 1, size=src.size) if weighted else None
     return csr_from_edges(n, src, dst, w, undirected=undirected)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU build of the same R-MAT graphs (gen/rmat_cuda.cu): bit-identical CSR, seconds
+# instead of minutes for the billion-edge graphs.
+
+_CUDA_SRC = os.path.join(_HERE, "rmat_cuda.cu")
+_CUDA_SO = os.path.join(_HERE, "libipg_gen_cuda.so")
+_cuda_handle = None
+
+
+def build_cuda(force: bool = False) -> str:
+    """Compile gen/rmat_cuda.cu for sm_103a (needs nvcc; no GPU needed to build)."""
+    if force or not os.path.exists(_CUDA_SO) or os.path.getmtime(_CUDA_SO) < os.path.getmtime(_CUDA_SRC):
+        nvcc = os.environ.get("NVCC") or "nvcc"
+        tmp = _CUDA_SO + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                               "-Xcompiler", "-fPIC", "-shared", _CUDA_SRC, "-o", tmp])
+        os.replace(tmp, _CUDA_SO)
+    return _CUDA_SO
+
+
+def _cuda_lib():
+    global _cuda_handle
+    if _cuda_handle is None:
+        if not os.path.exists(_CUDA_SO):
+            raise RuntimeError(f"{_CUDA_SO} is missing: build it with gen.build_cuda()")
+        lib = ctypes.CDLL(_CUDA_SO)
+        u32, u64, i32, dbl, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        lib.gen_rmat_cuda_plan.argtypes = [u32, u32, dbl, dbl, dbl, u64, i32, vp, ctypes.POINTER(vp),
+                                           ctypes.POINTER(u32), ctypes.POINTER(u64)]
+        lib.gen_rmat_cuda_plan.restype = i32
+        lib.gen_rmat_cuda_emit.argtypes = [vp, vp, vp, vp, u64, u32, vp]
+        lib.gen_rmat_cuda_emit.restype = i32
+        lib.gen_rmat_cuda_free.argtypes = [vp]
+        lib.gen_rmat_cuda_free.restype = None
+        _cuda_handle = lib
+    return _cuda_handle
+
+
+@dataclass
+class DeviceCSR:
+    """CSR held in torch CUDA tensors (offsets as int64 bit patterns of uint64, columns
+    and weights as int32 bit patterns of uint32)."""
+
+    n: int
+    m: int
+    offsets: "object"
+    cols: "object"
+    weights: "object" = None
+    directed: bool = True
+
+    def to_host(self, pinned: bool = False) -> CSR:
+        import torch
+
+        def cp(t, np_dtype):
+            if t is None:
+                return None
+            h = torch.empty(t.shape, dtype=t.dtype, pin_memory=pinned)
+            h.copy_(t)
+            return h.numpy().view(np_dtype)
+
+        return CSR(n=self.n, offsets=cp(self.offsets, np.uint64), cols=cp(self.cols, np.uint32),
+                   weights=cp(self.weights, np.uint32), directed=self.directed)
+
+
+def rmat_device(scale: int, edge_factor: int, seed: int = 1, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+                undirected: bool = False, weighted: bool = False, weight_seed: Optional[int] = None,
+                wmax: int = 255, device: int = 0) -> DeviceCSR:
+    """Same graph as ``rmat(...)``, built on a CUDA device into torch tensors."""
+    import torch
+
+    lib = _cuda_lib()
+    with torch.cuda.device(device):
+        stream = torch.cuda.current_stream()
+        sp = ctypes.c_void_p(int(stream.cuda_stream))
+        plan, n, m = ctypes.c_void_p(), ctypes.c_uint32(), ctypes.c_uint64()
+        torch.cuda.synchronize()
+        rc = lib.gen_rmat_cuda_plan(scale, edge_factor, a, b, c, seed & 0xFFFFFFFFFFFFFFFF, int(undirected), sp,
+                                    ctypes.byref(plan), ctypes.byref(n), ctypes.byref(m))
+        if rc != 0:
+            raise RuntimeError(f"gen_rmat_cuda_plan failed with code {rc}")
+        try:
+            offsets = torch.empty(n.value + 1, dtype=torch.int64, device="cuda")
+            cols = torch.empty(max(m.value, 1), dtype=torch.int32, device="cuda")
+            w = torch.empty(max(m.value, 1), dtype=torch.int32, device="cuda") if weighted else None
+            ws = default_weight_seed(seed) if weight_seed is None else weight_seed
+            rc = lib.gen_rmat_cuda_emit(plan, offsets.data_ptr(), cols.data_ptr(),
+                                        w.data_ptr() if w is not None else None, ws & 0xFFFFFFFFFFFFFFFF, wmax, sp)
+            if rc != 0:
+                raise RuntimeError(f"gen_rmat_cuda_emit failed with code {rc}")
+        finally:
+            lib.gen_rmat_cuda_free(plan)
+    return DeviceCSR(n=n.value, m=m.value, offsets=offsets, cols=cols[:m.value],
+                     weights=None if w is None else w[:m.value], directed=not undirected)

@@ -1,0 +1,161 @@
+/*
+ * ipg.h — C ABI of the GB300 Pregel superstep library (libipg.so).
+ *
+ * A Pregel program (Sec. I of the paper) runs in supersteps: every active
+ * vertex runs the compute step, sends messages along its out-edges, the
+ * messages are combined into each recipient's mailbox (Sec. III), and a vertex
+ * that received a message is active in the next superstep.  This library runs
+ * the paper's three benchmarks (Sec. VI-C) on one GPU:
+ *   PageRank            — pull ("single broadcast", Sec. IV) over the in-edges,
+ *                         sum combiner, FP32 ranks;
+ *   Hashmin components  — push with a min combiner over the active-vertex list
+ *                         ("selection bypass", Sec. VI-C);
+ *   SSSP                — push with a min combiner over the active-vertex list.
+ *
+ * Conventions for every call:
+ *   - Graphs are CSR: the out-edges of vertex u are columns[offsets[u] ..
+ *     offsets[u+1]-1]; offsets has n+1 entries, offsets[0] = 0,
+ *     offsets[n] = m, offsets non-decreasing, every column < n.  Self-loops and
+ *     parallel edges are allowed; each stored edge carries one message.
+ *   - Plain pointers and sizes only.  "host" pointers are ordinary CPU memory
+ *     (pinned memory makes copies faster); "dev" pointers are CUDA device
+ *     memory on the device that was current when the graph was created.
+ *   - A `stream` argument is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  *_dev calls enqueue on that stream and return after
+ *     the result is complete on it (the drivers read a few bytes back per
+ *     superstep to decide termination).
+ *   - Every call returns an ipg_status; on failure, ipg_last_error() gives a
+ *     message for the calling thread, outputs are unspecified and the stats
+ *     count is 0.
+ *   - A graph is not thread-safe: calls on one graph must not overlap (they
+ *     share the graph's device workspace).  Different graphs are independent.
+ *   - Memory: the library allocates the graph's device copy and workspace with
+ *     cudaMalloc and frees it in ipg_graph_destroy.  The caller owns every
+ *     buffer it passes in; the library never keeps a caller pointer.
+ */
+#ifndef IPG_H
+#define IPG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IPG_OK = 0,
+    IPG_EINVAL = 1,    /* bad argument or malformed CSR */
+    IPG_ENOMEM = 2,    /* device or pinned-host allocation failed */
+    IPG_ECUDA = 3,     /* a CUDA runtime call failed */
+    IPG_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+    IPG_EDEVICE = 5,   /* a kernel reported an internal inconsistency */
+    IPG_ENOTSUP = 6,   /* operation not supported for this graph */
+    IPG_EOVERFLOW = 7  /* an SSSP distance would reach UINT32_MAX */
+} ipg_status;
+
+typedef struct ipg_graph ipg_graph; /* opaque; owns its device copy */
+
+/* One record per superstep, numbered as in the Pregel model (superstep 0 is
+ * the one where every vertex is active). */
+typedef struct {
+    uint32_t superstep;
+    uint32_t flags;          /* IPG_STAT_* bits telling which fields were measured */
+    uint64_t active;         /* vertices that ran the compute step: n in superstep 0
+                                (and in every PageRank superstep), else the previous
+                                superstep's receivers; valid with IPG_STAT_RECEIVERS */
+    uint64_t senders;        /* vertices that broadcast to their out-neighbours */
+    uint64_t messages_sent;  /* messages sent = edges scanned from the senders */
+    uint64_t receivers;      /* distinct vertices that received >= 1 of those
+                                messages; valid with IPG_STAT_RECEIVERS */
+    float kernel_ms;         /* device time of the superstep's main kernel; valid with IPG_STAT_TIMING */
+    float superstep_ms;      /* device time of all of the superstep's kernels; valid with IPG_STAT_TIMING */
+} ipg_superstep_stats;
+
+#define IPG_STAT_RECEIVERS 1u /* count receivers (costs one extra atomic per message) */
+#define IPG_STAT_TIMING 2u    /* time every superstep with CUDA events */
+
+/* Caller-owned statistics buffer.  The library writes min(count, cap) records
+ * and sets `count` to the number of supersteps executed, which is also the
+ * superstep count of the Pregel run.  buf may be NULL when cap is 0. */
+typedef struct {
+    ipg_superstep_stats* buf;
+    uint32_t cap;
+    uint32_t count;  /* out */
+    uint32_t flags;  /* in: IPG_STAT_RECEIVERS | IPG_STAT_TIMING */
+    uint32_t reserved;
+} ipg_stats;
+
+/*
+ * ipg_graph_create — copy a host CSR graph to the current device.
+ *   offsets  host, n+1 entries;  columns host, m entries (may be NULL if m = 0);
+ *   weights  host, m entries or NULL (SSSP then uses length 1 per edge, the
+ *            paper's unweighted SSSP, Sec. VI-C);
+ *   directed nonzero: arbitrary directed graph.  zero: undirected, stored with
+ *            both directions of every edge (the paper's graphs, Sec. VI-B);
+ *            the library does not check the symmetry.
+ * The CSR is validated on the device; a malformed one returns IPG_EINVAL.
+ * The in-edge (CSC) copy needed by PageRank on a directed graph is built on
+ * the first ipg_pagerank call and kept.
+ */
+ipg_status ipg_graph_create(const uint64_t* offsets, const uint32_t* columns, const uint32_t* weights, uint32_t n,
+                            uint64_t m, int directed, ipg_graph** out);
+
+/* ipg_graph_create_dev — same from device arrays, copied on `stream`. */
+ipg_status ipg_graph_create_dev(const uint64_t* offsets_dev, const uint32_t* columns_dev,
+                                const uint32_t* weights_dev, uint32_t n, uint64_t m, int directed, void* stream,
+                                ipg_graph** out);
+
+/* Free the graph and all device memory it owns.  NULL is ignored. */
+void ipg_graph_destroy(ipg_graph* g);
+
+/* Sizes and kind of a graph (any output pointer may be NULL). */
+ipg_status ipg_graph_info(const ipg_graph* g, uint32_t* n, uint64_t* m, int* directed, int* weighted);
+
+/*
+ * ipg_pagerank — PageRank (Sec. VI-C), pull form over the in-edges ("single
+ * broadcast", Sec. IV): rank_0 = 1/n; for t = 1..updates,
+ *   rank_t(v) = 0.15/n + 0.85 * sum over edges u->v of rank_{t-1}(u)/outdeg(u);
+ * vertices without out-edges send nothing (their mass is dropped).
+ *   ranks_out  host, n floats (FP32), written on success.
+ * Sums are taken in a fixed order: results are bit-identical from run to run.
+ * Stats: updates+1 supersteps (superstep 0 only sends the initial ranks).
+ */
+ipg_status ipg_pagerank(ipg_graph* g, uint32_t updates, float* ranks_out, ipg_stats* stats);
+ipg_status ipg_pagerank_dev(ipg_graph* g, uint32_t updates, float* ranks_dev, ipg_stats* stats, void* stream);
+
+/*
+ * ipg_hashmin_cc — Hashmin connected components (Sec. VI-C, CC): every vertex
+ * starts with its own id, sends the smallest label it has seen to its
+ * neighbours whenever it drops, and the run ends when no message is sent.
+ *   labels_out  host, n uint32 (smallest vertex id of the component).
+ * Requires an undirected graph (directed = 0), else IPG_EINVAL.
+ */
+ipg_status ipg_hashmin_cc(ipg_graph* g, uint32_t* labels_out, ipg_stats* stats);
+ipg_status ipg_hashmin_cc_dev(ipg_graph* g, uint32_t* labels_dev, ipg_stats* stats, void* stream);
+
+/*
+ * ipg_sssp — single-source shortest paths (Sec. VI-C, SSSP) with a min
+ * combiner: the source starts at 0, every other vertex at UINT32_MAX
+ * (unreached); a vertex whose distance drops sends distance + w along each
+ * out-edge.  Edge lengths are the graph's weights, or 1 without weights.
+ *   source    vertex id < n, else IPG_EINVAL;
+ *   dist_out  host, n uint32 (UINT32_MAX = unreachable).
+ * A path length that would reach UINT32_MAX returns IPG_EOVERFLOW.
+ */
+ipg_status ipg_sssp(ipg_graph* g, uint32_t source, uint32_t* dist_out, ipg_stats* stats);
+ipg_status ipg_sssp_dev(ipg_graph* g, uint32_t source, uint32_t* dist_dev, ipg_stats* stats, void* stream);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char* ipg_last_error(void);
+
+/* Static name of a status code. */
+const char* ipg_status_string(ipg_status s);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int ipg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPG_H */

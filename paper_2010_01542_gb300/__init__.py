@@ -1,0 +1,287 @@
+"""GB300 Pregel superstep library: thin Python binding over ``libipg.so``.
+
+The C ABI is declared in ``include/ipg.h``; every function here has the same name
+as the C entry point it calls and only marshals arguments (numpy arrays for host
+buffers, torch CUDA tensors for device buffers, a torch stream for ``*_dev``
+calls).  All of the computation runs in the library's CUDA kernels; there is no
+CPU fallback.  If the library has not been built, importing a function that needs
+it raises ``IpgLibraryMissing``; build it with ``__graft_entry__.build()`` or
+``paper_2010_01542_gb300._build.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+from ._build import library_path
+
+__all__ = [
+    "IpgError", "IpgLibraryMissing", "SuperstepStats", "Graph", "ipg_graph_create", "ipg_graph_create_dev",
+    "ipg_graph_destroy", "ipg_graph_info", "ipg_pagerank", "ipg_pagerank_dev", "ipg_hashmin_cc",
+    "ipg_hashmin_cc_dev", "ipg_sssp", "ipg_sssp_dev", "ipg_last_error", "ipg_version",
+    "IPG_STAT_RECEIVERS", "IPG_STAT_TIMING", "INF", "load_library",
+]
+
+IPG_OK, IPG_EINVAL, IPG_ENOMEM, IPG_ECUDA, IPG_ETIMEOUT, IPG_EDEVICE, IPG_ENOTSUP, IPG_EOVERFLOW = range(8)
+STATUS_NAMES = ["IPG_OK", "IPG_EINVAL", "IPG_ENOMEM", "IPG_ECUDA", "IPG_ETIMEOUT", "IPG_EDEVICE", "IPG_ENOTSUP",
+                "IPG_EOVERFLOW"]
+IPG_STAT_RECEIVERS = 1
+IPG_STAT_TIMING = 2
+INF = 0xFFFFFFFF
+
+
+class IpgLibraryMissing(RuntimeError):
+    pass
+
+
+class IpgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+class _CStats(ctypes.Structure):
+    _fields_ = [("superstep", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("active", ctypes.c_uint64),
+                ("senders", ctypes.c_uint64), ("messages_sent", ctypes.c_uint64), ("receivers", ctypes.c_uint64),
+                ("kernel_ms", ctypes.c_float), ("superstep_ms", ctypes.c_float)]
+
+
+class _CStatsBuf(ctypes.Structure):
+    _fields_ = [("buf", ctypes.POINTER(_CStats)), ("cap", ctypes.c_uint32), ("count", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+@dataclass
+class SuperstepStats:
+    superstep: int
+    flags: int
+    active: int
+    senders: int
+    messages_sent: int
+    receivers: int
+    kernel_ms: float
+    superstep_ms: float
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load libipg.so (once).  Raises IpgLibraryMissing if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise IpgLibraryMissing(f"{p} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    pstats = ctypes.POINTER(_CStatsBuf)
+    lib.ipg_graph_create.argtypes = [vp, vp, vp, u32, u64, i32, ctypes.POINTER(vp)]
+    lib.ipg_graph_create_dev.argtypes = [vp, vp, vp, u32, u64, i32, vp, ctypes.POINTER(vp)]
+    lib.ipg_graph_destroy.argtypes = [vp]
+    lib.ipg_graph_destroy.restype = None
+    lib.ipg_graph_info.argtypes = [vp, ctypes.POINTER(u32), ctypes.POINTER(u64), ctypes.POINTER(i32),
+                                   ctypes.POINTER(i32)]
+    lib.ipg_pagerank.argtypes = [vp, u32, vp, pstats]
+    lib.ipg_pagerank_dev.argtypes = [vp, u32, vp, pstats, vp]
+    lib.ipg_hashmin_cc.argtypes = [vp, vp, pstats]
+    lib.ipg_hashmin_cc_dev.argtypes = [vp, vp, pstats, vp]
+    lib.ipg_sssp.argtypes = [vp, u32, vp, pstats]
+    lib.ipg_sssp_dev.argtypes = [vp, u32, vp, pstats, vp]
+    for f in ("ipg_graph_create", "ipg_graph_create_dev", "ipg_graph_info", "ipg_pagerank", "ipg_pagerank_dev",
+              "ipg_hashmin_cc", "ipg_hashmin_cc_dev", "ipg_sssp", "ipg_sssp_dev"):
+        getattr(lib, f).restype = i32
+    lib.ipg_last_error.argtypes = []
+    lib.ipg_last_error.restype = ctypes.c_char_p
+    lib.ipg_status_string.argtypes = [i32]
+    lib.ipg_status_string.restype = ctypes.c_char_p
+    lib.ipg_version.argtypes = []
+    lib.ipg_version.restype = i32
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def ipg_last_error() -> str:
+    return load_library().ipg_last_error().decode()
+
+
+def ipg_version() -> int:
+    return int(load_library().ipg_version())
+
+
+def _check(rc: int):
+    if rc != IPG_OK:
+        raise IpgError(rc, ipg_last_error())
+
+
+class Graph:
+    """Owning handle for an ``ipg_graph*``; destroyed with the object or by ``ipg_graph_destroy``."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("graph has been destroyed")
+        return self._h
+
+    def destroy(self):
+        if self._h:
+            load_library().ipg_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def info(self):
+        return ipg_graph_info(self)
+
+
+def _host_ptr(a: Optional[np.ndarray], dtype, count: int, what: str):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if a.size < count:
+        raise ValueError(f"{what} has {a.size} entries, needs {count}")
+    return a, (a.ctypes.data if a.size else None)
+
+
+def ipg_graph_create(offsets, columns, weights, n: int, m: int, directed: bool) -> Graph:
+    """Copy a host CSR graph (numpy arrays) to the current CUDA device."""
+    lib = load_library()
+    offs, po = _host_ptr(offsets, np.uint64, n + 1, "offsets")
+    cols, pc = _host_ptr(columns, np.uint32, m, "columns")
+    ws, pw = _host_ptr(weights, np.uint32, m, "weights")
+    h = ctypes.c_void_p()
+    _check(lib.ipg_graph_create(po, pc, pw, n, m, int(bool(directed)), ctypes.byref(h)))
+    return Graph(h)
+
+
+def _dev_ptr(t, itemsize: int, count: int, what: str):
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous() or t.element_size() != itemsize:
+        raise ValueError(f"{what} must be contiguous with {itemsize}-byte elements")
+    if t.numel() < count:
+        raise ValueError(f"{what} has {t.numel()} entries, needs {count}")
+    return t.data_ptr() if count else None
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def ipg_graph_create_dev(offsets, columns, weights, n: int, m: int, directed: bool, stream=None) -> Graph:
+    """Copy a device CSR graph (torch CUDA tensors: 8-byte offsets, 4-byte columns/weights)."""
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.ipg_graph_create_dev(_dev_ptr(offsets, 8, n + 1, "offsets"), _dev_ptr(columns, 4, m, "columns"),
+                                    _dev_ptr(weights, 4, m, "weights"), n, m, int(bool(directed)),
+                                    _stream_ptr(stream), ctypes.byref(h)))
+    return Graph(h)
+
+
+def ipg_graph_destroy(g: Graph) -> None:
+    g.destroy()
+
+
+def ipg_graph_info(g: Graph):
+    n, m, d, w = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().ipg_graph_info(g.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(d),
+                                         ctypes.byref(w)))
+    return {"n": n.value, "m": m.value, "directed": bool(d.value), "weighted": bool(w.value)}
+
+
+class _Stats:
+    def __init__(self, flags: int, cap: int):
+        self.arr = (_CStats * max(cap, 1))()
+        self.c = _CStatsBuf(ctypes.cast(self.arr, ctypes.POINTER(_CStats)), cap, 0, flags, 0)
+
+    def result(self) -> List[SuperstepStats]:
+        k = min(self.c.count, self.c.cap)
+        return [SuperstepStats(int(s.superstep), int(s.flags), int(s.active), int(s.senders),
+                               int(s.messages_sent), int(s.receivers), float(s.kernel_ms), float(s.superstep_ms))
+                for s in self.arr[:k]]
+
+
+def _run(fn, args, stats_flags: int, stats_cap: int):
+    st = _Stats(stats_flags, stats_cap)
+    _check(fn(*args, ctypes.byref(st.c)))
+    return int(st.c.count), st.result()
+
+
+def _run_dev(fn, args, stats_flags: int, stats_cap: int, stream):
+    st = _Stats(stats_flags, stats_cap)
+    _check(fn(*args, ctypes.byref(st.c), _stream_ptr(stream)))
+    return int(st.c.count), st.result()
+
+
+def ipg_pagerank(g: Graph, updates: int, ranks_out: Optional[np.ndarray] = None, stats_flags: int = 0,
+                 stats_cap: int = 4096):
+    """PageRank into a host float32 array.  Returns (ranks, supersteps, stats)."""
+    n = ipg_graph_info(g)["n"]
+    out = np.empty(n, dtype=np.float32) if ranks_out is None else ranks_out
+    if out.dtype != np.float32 or not out.flags.c_contiguous or out.size < n:
+        raise ValueError("ranks_out must be a contiguous float32 array of n entries")
+    count, stats = _run(load_library().ipg_pagerank, (g.handle, updates, out.ctypes.data if n else None),
+                        stats_flags, stats_cap)
+    return out, count, stats
+
+
+def ipg_pagerank_dev(g: Graph, updates: int, ranks_dev, stats_flags: int = 0, stats_cap: int = 4096, stream=None):
+    """PageRank into a CUDA float32 tensor on `stream`.  Returns (supersteps, stats)."""
+    n = ipg_graph_info(g)["n"]
+    return _run_dev(load_library().ipg_pagerank_dev, (g.handle, updates, _dev_ptr(ranks_dev, 4, n, "ranks")),
+                    stats_flags, stats_cap, stream)
+
+
+def ipg_hashmin_cc(g: Graph, labels_out: Optional[np.ndarray] = None, stats_flags: int = 0, stats_cap: int = 1 << 16):
+    """Hashmin components into a host uint32 array.  Returns (labels, supersteps, stats)."""
+    n = ipg_graph_info(g)["n"]
+    out = np.empty(n, dtype=np.uint32) if labels_out is None else labels_out
+    if out.dtype != np.uint32 or not out.flags.c_contiguous or out.size < n:
+        raise ValueError("labels_out must be a contiguous uint32 array of n entries")
+    count, stats = _run(load_library().ipg_hashmin_cc, (g.handle, out.ctypes.data if n else None), stats_flags,
+                        stats_cap)
+    return out, count, stats
+
+
+def ipg_hashmin_cc_dev(g: Graph, labels_dev, stats_flags: int = 0, stats_cap: int = 1 << 16, stream=None):
+    n = ipg_graph_info(g)["n"]
+    return _run_dev(load_library().ipg_hashmin_cc_dev, (g.handle, _dev_ptr(labels_dev, 4, n, "labels")),
+                    stats_flags, stats_cap, stream)
+
+
+def ipg_sssp(g: Graph, source: int, dist_out: Optional[np.ndarray] = None, stats_flags: int = 0,
+             stats_cap: int = 1 << 16):
+    """SSSP into a host uint32 array (INF = unreachable).  Returns (dist, supersteps, stats)."""
+    n = ipg_graph_info(g)["n"]
+    out = np.empty(n, dtype=np.uint32) if dist_out is None else dist_out
+    if out.dtype != np.uint32 or not out.flags.c_contiguous or out.size < n:
+        raise ValueError("dist_out must be a contiguous uint32 array of n entries")
+    count, stats = _run(load_library().ipg_sssp, (g.handle, source, out.ctypes.data if n else None), stats_flags,
+                        stats_cap)
+    return out, count, stats
+
+
+def ipg_sssp_dev(g: Graph, source: int, dist_dev, stats_flags: int = 0, stats_cap: int = 1 << 16, stream=None):
+    n = ipg_graph_info(g)["n"]
+    return _run_dev(load_library().ipg_sssp_dev, (g.handle, source, _dev_ptr(dist_dev, 4, n, "dist")),
+                    stats_flags, stats_cap, stream)

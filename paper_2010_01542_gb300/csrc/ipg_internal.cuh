@@ -1,0 +1,131 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ipg.h"
+
+namespace ipg {
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+
+// device status word bits (written by kernels, read by the host after a run)
+constexpr uint32_t kStatusOverflow = 1u;    // an SSSP distance reached UINT32_MAX
+constexpr uint32_t kStatusBadCsr = 2u;      // validation: offsets not monotone / wrong ends
+constexpr uint32_t kStatusBadColumn = 4u;   // validation: a column >= n
+constexpr uint32_t kStatusInternal = 8u;    // a kernel found an inconsistent index
+
+// counters the push drivers read back every superstep (one 64-byte block)
+struct PushCounters {
+    unsigned long long edges;      // messages of the current superstep (sum of frontier degrees)
+    unsigned long long receivers;  // distinct receivers (stats mode)
+    unsigned int next_size;        // vertices appended to the next frontier
+    unsigned int tiles;            // merge-path tiles of the current superstep
+    unsigned int status;           // kStatus* bits
+    unsigned int pad[9];
+};
+
+ipg_status set_error(ipg_status s, const char* fmt, ...);
+ipg_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define IPG_CUDA(call)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return ::ipg::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define IPG_TRY(expr)                          \
+    do {                                       \
+        ipg_status s_ = (expr);                \
+        if (s_ != IPG_OK) return s_;           \
+    } while (0)
+
+// grows a device buffer (contents are not kept)
+ipg_status ensure_buffer(void** p, size_t* cap, size_t bytes);
+
+template <typename T>
+inline ipg_status ensure(T** p, size_t* cap, size_t count) {
+    return ensure_buffer(reinterpret_cast<void**>(p), cap, count * sizeof(T));
+}
+
+// RAII guard: makes the graph's device current for the duration of a call
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// per-superstep CUDA events (IPG_STAT_TIMING)
+struct StepTimer {
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    ipg_status init();
+    void destroy();
+};
+
+}  // namespace ipg
+
+struct ipg_graph {
+    int device = 0;
+    uint32_t n = 0;
+    uint64_t m = 0;
+    int directed = 1;
+    int weighted = 0;
+
+    // CSR (out-edges)
+    uint64_t* off = nullptr;
+    uint32_t* col = nullptr;
+    uint32_t* w = nullptr;
+
+    // CSC (in-edges) for pull; aliases the CSR on undirected graphs
+    uint64_t* csc_off = nullptr;
+    uint32_t* csc_src = nullptr;
+    bool csc_ready = false;
+    bool csc_owned = false;
+    long long in_nonempty = -1;  // vertices with in-degree > 0 (PageRank receivers), lazily counted
+
+    // PageRank state
+    float* inv_outdeg = nullptr;
+    float* pr_box[2] = {nullptr, nullptr};  // outbox double buffer
+    uint32_t* pr_tile_row = nullptr;        // merge-path tile boundaries over the CSC
+    float* pr_head = nullptr;               // per tile: partial sum of the row that began in an earlier tile
+    float* pr_tail = nullptr;               // per tile: partial sum of the row that continues past it
+    uint64_t pr_tiles = 0;
+    float* pr_out_stage = nullptr;          // host-variant output staging
+    size_t pr_out_stage_cap = 0;
+
+    // push (Hashmin / SSSP) workspace
+    uint32_t* stamp = nullptr;       // superstep in which the vertex was last appended to a frontier
+    uint32_t* rstamp = nullptr;      // superstep in which the vertex last received (stats mode)
+    uint32_t* frontier[2] = {nullptr, nullptr};
+    unsigned long long* fr_prefix = nullptr;  // exclusive prefix of frontier out-degrees (f+1)
+    unsigned long long* fr_rowstart = nullptr;
+    uint32_t* fr_val = nullptr;               // value snapshot of each frontier vertex
+    unsigned long long* block_sums = nullptr;
+    size_t block_sums_cap = 0;
+    uint32_t* push_tile_row = nullptr;
+    size_t push_tile_cap = 0;
+    uint32_t* val_stage = nullptr;            // host-variant value buffer
+    ipg::PushCounters* counters = nullptr;    // device
+    ipg::PushCounters* h_counters = nullptr;  // pinned host mirror
+
+    cudaStream_t stream = nullptr;  // used by the host-buffer entry points
+    ipg::StepTimer timer;
+};
+
+namespace ipg {
+// in ipg_graph.cu
+ipg_status ensure_csc(ipg_graph* g, cudaStream_t st);
+ipg_status count_in_nonempty(ipg_graph* g, cudaStream_t st);
+ipg_status ensure_push_workspace(ipg_graph* g, bool receivers);
+// stats helpers
+void stats_begin(ipg_stats* s);
+void stats_put(ipg_stats* s, uint32_t idx, const ipg_superstep_stats& rec);
+}  // namespace ipg

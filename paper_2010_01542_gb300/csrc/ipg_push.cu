@@ -1,0 +1,510 @@
+// Push supersteps with a min combiner: Hashmin connected components and SSSP
+// (Sec. VI-C).  Both keep an explicit list of the vertices that send in the
+// current superstep — the paper's "selection bypass" — instead of scanning
+// every vertex.
+//
+// One superstep s, given the frontier F_s (vertices whose value dropped in
+// s-1, or the initial senders in superstep 0):
+//   prepare    out-degree of every frontier vertex, an exclusive prefix sum of
+//              those degrees (two passes plus a single-CTA scan of the block
+//              sums), and a snapshot of each sender's value and row start;
+//   partition  merge-path split of (frontier rows + their edges) into tiles of
+//              2048 items, so a hub's edges are spread over many CTAs and the
+//              split costs one short binary search per tile (the paper's
+//              edge-centric split had to be recomputed every superstep and lost
+//              on small graphs, Sec. VII-A);
+//   relax      one thread per edge: candidate = sender value (+ weight for
+//              SSSP); if it is below the receiver's current value, atomicMin.
+//              For a u32 min the hardware atomic is the whole combiner: it is
+//              lock-free and has no empty-mailbox ambiguity (Sec. III), because
+//              the value array itself is the mailbox and only a strict drop
+//              activates the receiver.  A thread whose atomicMin lowered the
+//              value claims the receiver for F_{s+1} with a per-vertex stamp,
+//              and the warp appends its claims with one atomicAdd (ballot +
+//              popc).
+// Senders' values are snapshotted before the relax kernel, so a value that drops
+// during superstep s is sent only in s+1: the run is the synchronous Pregel
+// execution, superstep for superstep, and the per-superstep counts match the
+// model exactly.
+#include "ipg_internal.cuh"
+
+namespace ipg {
+namespace {
+
+constexpr int kFrThreads = 256;
+constexpr int kFrItems = 8;
+constexpr uint32_t kFrBlock = kFrThreads * kFrItems;
+constexpr int kScanThreads = 1024;
+constexpr int kPushThreads = 256;
+constexpr uint32_t kPushTile = 2048;
+
+enum Kind { kHashmin = 0, kSssp = 1 };
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long* s_tmp) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_tmp[warp] = x;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += s_tmp[q];
+    return t;  // valid in thread 0
+}
+
+// exclusive block scan of one u64 per thread; returns this thread's prefix, *total = block total
+__device__ __forceinline__ unsigned long long block_exscan_u64(unsigned long long x, unsigned long long* s_tmp,
+                                                               unsigned long long* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    unsigned long long incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < nw ? s_tmp[lane] : 0;
+        unsigned long long wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) s_tmp[lane] = wi - w;  // exclusive warp offsets
+        if (lane == nw - 1) s_tmp[32] = wi;
+    }
+    __syncthreads();
+    *total = s_tmp[32];
+    return s_tmp[warp] + incl - x;
+}
+
+__global__ void hashmin_init_kernel(uint32_t* __restrict__ val, uint32_t* __restrict__ frontier, uint32_t n) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        val[v] = (uint32_t)v;
+        frontier[v] = (uint32_t)v;
+    }
+}
+
+__global__ void sssp_init_kernel(uint32_t* __restrict__ val, uint32_t* __restrict__ frontier, uint32_t n,
+                                 uint32_t source) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        val[v] = v == source ? 0u : kInf;
+    if (blockIdx.x == 0 && threadIdx.x == 0) frontier[0] = source;
+}
+
+// pass 1 of the frontier prefix: one degree total per block of 2048 entries
+__global__ void __launch_bounds__(kFrThreads) fr_reduce_kernel(const uint32_t* __restrict__ F, uint32_t f,
+                                                               const uint64_t* __restrict__ off,
+                                                               unsigned long long* __restrict__ block_sums) {
+    __shared__ unsigned long long s_tmp[33];
+    const uint64_t b0 = (uint64_t)blockIdx.x * kFrBlock;
+    unsigned long long d = 0;
+#pragma unroll
+    for (int q = 0; q < kFrItems; ++q) {
+        uint64_t i = b0 + (uint64_t)q * kFrThreads + threadIdx.x;
+        if (i < f) {
+            uint32_t u = F[i];
+            d += off[u + 1] - off[u];
+        }
+    }
+    unsigned long long t = block_sum_u64(d, s_tmp);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = t;
+}
+
+// single CTA: exclusive scan of the block totals, edge count and tile count
+__global__ void __launch_bounds__(kScanThreads) fr_scan_kernel(unsigned long long* __restrict__ block_sums,
+                                                               uint32_t nb, uint32_t f,
+                                                               unsigned long long* __restrict__ prefix,
+                                                               PushCounters* __restrict__ ctr) {
+    __shared__ unsigned long long s_tmp[33];
+    const uint32_t per = (nb + kScanThreads - 1) / kScanThreads;
+    const uint64_t a = (uint64_t)threadIdx.x * per;
+    const uint64_t b = a + per < nb ? a + per : nb;
+    unsigned long long s = 0;
+    for (uint64_t i = a; i < b; ++i) s += block_sums[i];
+    unsigned long long total;
+    unsigned long long run = block_exscan_u64(s, s_tmp, &total);
+    for (uint64_t i = a; i < b; ++i) {
+        unsigned long long x = block_sums[i];
+        block_sums[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 0) {
+        prefix[f] = total;
+        ctr->edges = total;
+        ctr->tiles = (unsigned)(((unsigned long long)f + total + kPushTile - 1) / kPushTile);
+        ctr->next_size = 0;
+        ctr->receivers = 0;
+    }
+}
+
+// pass 2: per-entry exclusive prefix, row start and value snapshot
+__global__ void __launch_bounds__(kFrThreads) fr_write_kernel(
+    const uint32_t* __restrict__ F, uint32_t f, const uint64_t* __restrict__ off, const uint32_t* __restrict__ val,
+    const unsigned long long* __restrict__ block_off, unsigned long long* __restrict__ prefix,
+    unsigned long long* __restrict__ rowstart, uint32_t* __restrict__ fval) {
+    __shared__ unsigned long long s_tmp[33];
+    const uint64_t i0 = (uint64_t)blockIdx.x * kFrBlock + (uint64_t)threadIdx.x * kFrItems;
+    uint64_t st[kFrItems];
+    unsigned long long deg[kFrItems];
+    unsigned long long local = 0;
+#pragma unroll
+    for (int q = 0; q < kFrItems; ++q) {
+        uint64_t i = i0 + q;
+        deg[q] = 0;
+        st[q] = 0;
+        if (i < f) {
+            uint32_t u = F[i];
+            st[q] = off[u];
+            deg[q] = off[u + 1] - st[q];
+            fval[i] = val[u];
+        }
+        local += deg[q];
+    }
+    unsigned long long total;
+    unsigned long long run = block_exscan_u64(local, s_tmp, &total) + block_off[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < kFrItems; ++q) {
+        uint64_t i = i0 + q;
+        if (i < f) {
+            prefix[i] = run;
+            rowstart[i] = st[q];
+        }
+        run += deg[q];
+    }
+}
+
+__device__ __forceinline__ uint32_t merge_path_rows(const unsigned long long* __restrict__ row_end, uint32_t nrows,
+                                                    uint64_t nedges, uint64_t diag) {
+    uint64_t lo = diag > nedges ? diag - nedges : 0;
+    uint64_t hi = diag < nrows ? diag : nrows;
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) >> 1;
+        if (row_end[mid] <= diag - mid - 1)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (uint32_t)lo;
+}
+
+__global__ void push_partition_kernel(const unsigned long long* __restrict__ prefix, uint32_t f,
+                                      const PushCounters* __restrict__ ctr, uint32_t* __restrict__ tile_row) {
+    const uint64_t E = ctr->edges;
+    const uint64_t tiles = ctr->tiles;
+    const uint64_t total = (uint64_t)f + E;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= tiles; t += stride) {
+        uint64_t diag = t * kPushTile;
+        if (diag > total) diag = total;
+        tile_row[t] = merge_path_rows(prefix + 1, f, E, diag);
+    }
+}
+
+template <int kKind, bool kWeighted, bool kRecv>
+__global__ void __launch_bounds__(kPushThreads) push_relax_kernel(
+    const unsigned long long* __restrict__ prefix, const unsigned long long* __restrict__ rowstart,
+    const uint32_t* __restrict__ fval, const uint32_t* __restrict__ tile_row, const uint32_t* __restrict__ col,
+    const uint32_t* __restrict__ wt, uint32_t* __restrict__ val, uint32_t* __restrict__ stamp,
+    uint32_t* __restrict__ rstamp, uint32_t* __restrict__ next, PushCounters* __restrict__ ctr, uint32_t f,
+    uint32_t tag) {
+    __shared__ uint32_t s_start[kPushTile + 1];
+    __shared__ unsigned long long s_base[kPushTile + 1];
+    __shared__ uint32_t s_val[kPushTile + 1];
+    const uint64_t E = ctr->edges;
+    const uint32_t tiles = ctr->tiles;
+    const uint64_t total = (uint64_t)f + E;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    for (uint32_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const uint64_t d0 = (uint64_t)tile * kPushTile;
+        const uint64_t d1 = d0 + kPushTile < total ? d0 + kPushTile : total;
+        const uint32_t i0 = tile_row[tile];
+        const uint32_t i1 = tile_row[tile + 1];
+        const uint64_t j0 = d0 - i0;
+        const uint32_t R = i1 - i0;
+        const uint32_t Et = (uint32_t)((d1 - i1) - j0);
+        __syncthreads();  // the previous tile is done with shared memory
+        for (uint32_t k = tid; k <= R; k += kPushThreads) {
+            const uint32_t r = i0 + k;
+            if (r < f) {
+                const unsigned long long p = prefix[r];
+                s_start[k] = p > j0 ? (uint32_t)(p - j0) : 0u;
+                s_base[k] = rowstart[r] + (j0 - p);  // edge position = base + k (mod 2^64)
+                s_val[k] = fval[r];
+            } else {
+                s_start[k] = Et + 1;
+                s_base[k] = 0;
+                s_val[k] = 0;
+            }
+        }
+        __syncthreads();
+        for (uint32_t k0 = 0; k0 < Et; k0 += kPushThreads) {
+            const uint32_t k = k0 + tid;
+            bool app = false, rcv = false;
+            uint32_t v = 0;
+            if (k < Et) {
+                // row of edge k: last row whose start is <= k
+                uint32_t lo = 0, hi = R;
+                while (lo < hi) {
+                    uint32_t mid = (lo + hi + 1) >> 1;
+                    if (s_start[mid] <= k)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                const unsigned long long p = s_base[lo] + k;
+                v = __ldcs(col + p);
+                uint32_t cand;
+                if (kKind == kHashmin) {
+                    cand = s_val[lo];
+                } else {
+                    unsigned long long d = (unsigned long long)s_val[lo] + (kWeighted ? __ldcs(wt + p) : 1u);
+                    if (d >= kInf) {
+                        atomicOr(&ctr->status, kStatusOverflow);
+                        d = kInf - 1;
+                    }
+                    cand = (uint32_t)d;
+                }
+                if (kRecv) rcv = atomicExch(&rstamp[v], tag) != tag;
+                const uint32_t cur = val[v];  // may be stale-high, never below the true value
+                if (cand < cur) {
+                    const uint32_t old = atomicMin(&val[v], cand);
+                    if (cand < old) app = atomicExch(&stamp[v], tag) != tag;
+                }
+            }
+            const unsigned mask = __ballot_sync(0xFFFFFFFFu, app);
+            if (mask) {
+                const int leader = __ffs(mask) - 1;
+                uint32_t pos = 0;
+                if (lane == leader) pos = atomicAdd(&ctr->next_size, (unsigned)__popc(mask));
+                pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+                if (app) next[pos + __popc(mask & ((1u << lane) - 1u))] = v;
+            }
+            if (kRecv) {
+                const unsigned rm = __ballot_sync(0xFFFFFFFFu, rcv);
+                if (lane == 0 && rm) atomicAdd(&ctr->receivers, (unsigned long long)__popc(rm));
+            }
+        }
+    }
+}
+
+unsigned grid_cap(uint64_t work, unsigned cap = 152 * 16) {
+    uint64_t b = (work + 255) / 256;
+    if (b < 1) b = 1;
+    return (unsigned)(b < cap ? b : cap);
+}
+
+int sm_count(int dev) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    return v;
+}
+
+template <int kKind, bool kWeighted, bool kRecv>
+void launch_relax(unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next, uint32_t f,
+                  uint32_t tag) {
+    push_relax_kernel<kKind, kWeighted, kRecv><<<grid, kPushThreads, 0, st>>>(
+        g->fr_prefix, g->fr_rowstart, g->fr_val, g->push_tile_row, g->col, g->w, val, g->stamp, g->rstamp, next,
+        g->counters, f, tag);
+}
+
+void relax_dispatch(int kind, bool weighted, bool recv, unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val,
+                    uint32_t* next, uint32_t f, uint32_t tag) {
+    if (kind == kHashmin) {
+        if (recv)
+            launch_relax<kHashmin, false, true>(grid, st, g, val, next, f, tag);
+        else
+            launch_relax<kHashmin, false, false>(grid, st, g, val, next, f, tag);
+    } else if (weighted) {
+        if (recv)
+            launch_relax<kSssp, true, true>(grid, st, g, val, next, f, tag);
+        else
+            launch_relax<kSssp, true, false>(grid, st, g, val, next, f, tag);
+    } else {
+        if (recv)
+            launch_relax<kSssp, false, true>(grid, st, g, val, next, f, tag);
+        else
+            launch_relax<kSssp, false, false>(grid, st, g, val, next, f, tag);
+    }
+}
+
+ipg_status ensure_events_push(size_t count, cudaEvent_t** evs) {
+    static thread_local cudaEvent_t* ev = nullptr;
+    static thread_local size_t cap = 0;
+    if (count > cap) {
+        cudaEvent_t* nv = new cudaEvent_t[count];
+        for (size_t i = 0; i < cap; ++i) nv[i] = ev[i];
+        for (size_t i = cap; i < count; ++i) IPG_CUDA(cudaEventCreate(&nv[i]));
+        delete[] ev;
+        ev = nv;
+        cap = count;
+    }
+    *evs = ev;
+    return IPG_OK;
+}
+
+ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* val, ipg_stats* stats, cudaStream_t st) {
+    stats_begin(stats);
+    const char* name = kind == kHashmin ? "ipg_hashmin_cc" : "ipg_sssp";
+    if (!g) return set_error(IPG_EINVAL, "%s: graph is NULL", name);
+    if (kind == kHashmin && g->directed)
+        return set_error(IPG_EINVAL, "%s: Hashmin components need an undirected graph (directed = 0)", name);
+    if (kind == kSssp && source >= g->n) return set_error(IPG_EINVAL, "%s: source %u >= n = %u", name, source, g->n);
+    if (g->n && !val) return set_error(IPG_EINVAL, "%s: output is NULL", name);
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return set_error(IPG_ECUDA, "%s: cannot select the graph's device", name);
+    const uint32_t n = g->n;
+    const bool recv = stats && (stats->flags & IPG_STAT_RECEIVERS);
+    const bool timing = stats && (stats->flags & IPG_STAT_TIMING);
+    if (n == 0) {  // superstep 0 runs on no vertex and sends nothing
+        if (stats) {
+            ipg_superstep_stats r{};
+            r.flags = recv ? IPG_STAT_RECEIVERS : 0u;
+            stats_put(stats, 0, r);
+            stats->count = 1;
+        }
+        return IPG_OK;
+    }
+    IPG_TRY(ensure_push_workspace(g, recv));
+    cudaEvent_t* ev = nullptr;
+    if (timing) IPG_TRY(ensure_events_push(3, &ev));
+    const int sms = sm_count(g->device);
+    const unsigned relax_grid = (unsigned)sms * 6;
+    const unsigned part_grid = (unsigned)sms * 2;
+
+    IPG_CUDA(cudaMemsetAsync(g->stamp, 0, sizeof(uint32_t) * n, st));
+    if (recv) IPG_CUDA(cudaMemsetAsync(g->rstamp, 0, sizeof(uint32_t) * n, st));
+    IPG_CUDA(cudaMemsetAsync(&g->counters->status, 0, sizeof(unsigned), st));
+    uint32_t f;
+    if (kind == kHashmin) {
+        hashmin_init_kernel<<<grid_cap(n), 256, 0, st>>>(val, g->frontier[0], n);
+        f = n;
+    } else {
+        sssp_init_kernel<<<grid_cap(n), 256, 0, st>>>(val, g->frontier[0], n, source);
+        f = 1;
+    }
+    IPG_CUDA(cudaGetLastError());
+
+    int cur = 0;
+    uint32_t s = 0;
+    uint64_t prev_receivers = 0;
+    uint32_t count = 0;
+    for (;;) {
+        const uint32_t nb = (f + kFrBlock - 1) / kFrBlock;
+        if (timing) IPG_CUDA(cudaEventRecord(ev[0], st));
+        fr_reduce_kernel<<<nb, kFrThreads, 0, st>>>(g->frontier[cur], f, g->off, g->block_sums);
+        fr_scan_kernel<<<1, kScanThreads, 0, st>>>(g->block_sums, nb, f, g->fr_prefix, g->counters);
+        fr_write_kernel<<<nb, kFrThreads, 0, st>>>(g->frontier[cur], f, g->off, val, g->block_sums, g->fr_prefix,
+                                                   g->fr_rowstart, g->fr_val);
+        push_partition_kernel<<<part_grid, 256, 0, st>>>(g->fr_prefix, f, g->counters, g->push_tile_row);
+        IPG_CUDA(cudaGetLastError());
+        if (timing) IPG_CUDA(cudaEventRecord(ev[1], st));
+        relax_dispatch(kind, g->weighted != 0, recv, relax_grid, st, g, val, g->frontier[cur ^ 1], f, s + 1);
+        IPG_CUDA(cudaGetLastError());
+        if (timing) IPG_CUDA(cudaEventRecord(ev[2], st));
+        IPG_CUDA(cudaMemcpyAsync(g->h_counters, g->counters, sizeof(PushCounters), cudaMemcpyDeviceToHost, st));
+        IPG_CUDA(cudaStreamSynchronize(st));
+        const PushCounters h = *g->h_counters;
+        if (h.status & kStatusOverflow) {
+            if (stats) stats->count = 0;
+            return set_error(IPG_EOVERFLOW, "%s: a path length reached UINT32_MAX", name);
+        }
+        if (stats) {
+            ipg_superstep_stats r{};
+            r.superstep = s;
+            r.flags = (recv ? IPG_STAT_RECEIVERS : 0u) | (timing ? IPG_STAT_TIMING : 0u);
+            r.active = s == 0 ? n : (recv ? prev_receivers : 0);
+            r.senders = f;
+            r.messages_sent = h.edges;
+            r.receivers = recv ? h.receivers : 0;
+            if (timing) {
+                cudaEventElapsedTime(&r.kernel_ms, ev[1], ev[2]);
+                cudaEventElapsedTime(&r.superstep_ms, ev[0], ev[2]);
+            }
+            stats_put(stats, s, r);
+        }
+        if (h.next_size == 0) {
+            count = s + 1;
+            if (h.edges > 0) {  // the receivers still run one more superstep, change nothing, send nothing
+                if (stats) {
+                    ipg_superstep_stats r{};
+                    r.superstep = s + 1;
+                    r.flags = recv ? IPG_STAT_RECEIVERS : 0u;
+                    r.active = recv ? h.receivers : 0;
+                    stats_put(stats, s + 1, r);
+                }
+                count = s + 2;
+            }
+            break;
+        }
+        if (h.next_size > n) return set_error(IPG_EDEVICE, "%s: frontier overflow (%u > n)", name, h.next_size);
+        prev_receivers = h.receivers;
+        f = h.next_size;
+        cur ^= 1;
+        ++s;
+    }
+    if (stats) stats->count = count;
+    return IPG_OK;
+}
+
+}  // namespace
+
+ipg_status ensure_push_workspace(ipg_graph* g, bool receivers) {
+    const uint32_t n = g->n;
+    if (!g->stamp) {
+        IPG_CUDA(cudaMalloc(&g->stamp, sizeof(uint32_t) * n));
+        IPG_CUDA(cudaMalloc(&g->frontier[0], sizeof(uint32_t) * n));
+        IPG_CUDA(cudaMalloc(&g->frontier[1], sizeof(uint32_t) * n));
+        IPG_CUDA(cudaMalloc(&g->fr_prefix, sizeof(unsigned long long) * ((size_t)n + 1)));
+        IPG_CUDA(cudaMalloc(&g->fr_rowstart, sizeof(unsigned long long) * n));
+        IPG_CUDA(cudaMalloc(&g->fr_val, sizeof(uint32_t) * n));
+        const size_t nb = ((size_t)n + kFrBlock - 1) / kFrBlock;
+        IPG_TRY(ensure(&g->block_sums, &g->block_sums_cap, nb + 1));
+        const size_t tiles = ((size_t)n + g->m + kPushTile - 1) / kPushTile + 2;
+        IPG_TRY(ensure(&g->push_tile_row, &g->push_tile_cap, tiles + 1));
+    }
+    if (receivers && !g->rstamp) IPG_CUDA(cudaMalloc(&g->rstamp, sizeof(uint32_t) * n));
+    return IPG_OK;
+}
+
+}  // namespace ipg
+
+using namespace ipg;
+
+extern "C" {
+
+ipg_status ipg_hashmin_cc_dev(ipg_graph* g, uint32_t* labels_dev, ipg_stats* stats, void* stream) {
+    return push_run(g, kHashmin, 0, labels_dev, stats, (cudaStream_t)stream);
+}
+
+ipg_status ipg_sssp_dev(ipg_graph* g, uint32_t source, uint32_t* dist_dev, ipg_stats* stats, void* stream) {
+    return push_run(g, kSssp, source, dist_dev, stats, (cudaStream_t)stream);
+}
+
+static ipg_status host_variant(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_stats* stats) {
+    stats_begin(stats);
+    if (!g) return set_error(IPG_EINVAL, "graph is NULL");
+    if (g->n && !out) return set_error(IPG_EINVAL, "output is NULL");
+    DeviceGuard guard(g->device);
+    size_t cap = g->val_stage ? (size_t)g->n * sizeof(uint32_t) : 0;
+    if (!g->val_stage) IPG_TRY(ensure(&g->val_stage, &cap, (size_t)g->n));
+    IPG_TRY(push_run(g, kind, source, g->val_stage, stats, g->stream));
+    if (g->n) {
+        IPG_CUDA(cudaMemcpyAsync(out, g->val_stage, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost, g->stream));
+        IPG_CUDA(cudaStreamSynchronize(g->stream));
+    }
+    return IPG_OK;
+}
+
+ipg_status ipg_hashmin_cc(ipg_graph* g, uint32_t* labels_out, ipg_stats* stats) {
+    return host_variant(g, kHashmin, 0, labels_out, stats);
+}
+
+ipg_status ipg_sssp(ipg_graph* g, uint32_t source, uint32_t* dist_out, ipg_stats* stats) {
+    return host_variant(g, kSssp, source, dist_out, stats);
+}
+
+}  // extern "C"

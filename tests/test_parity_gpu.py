@@ -1,0 +1,319 @@
+"""CUDA path vs the CPU oracle, through the C ABI.
+
+Bars: Hashmin labels, SSSP distances, superstep counts and every per-superstep
+count (active, senders, messages sent, receivers) are bit-exact; FP32 PageRank is
+within max|d rank| / max(rank_oracle) <= 1e-5 of the float64 oracle and
+bit-identical from run to run.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+PR_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ipg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2010_01542_gb300 as ipg
+    from paper_2010_01542_gb300 import _build
+
+    _build.build()
+    ipg.load_library()
+    return ipg
+
+
+def _create(ipg, g, directed=None):
+    d = g.directed if directed is None else directed
+    return ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, d)
+
+
+def _cmp_stats(gpu_stats, gpu_count, orc):
+    assert gpu_count == orc.supersteps
+    assert len(gpu_stats) == len(orc.stats)
+    for a, b in zip(gpu_stats, orc.stats):
+        assert (a.superstep, a.senders, a.messages_sent, a.receivers, a.active) == \
+               (b.superstep, b.senders, b.messages_sent, b.receivers, b.active), (a, b)
+
+
+def check_pagerank(ipg, g, updates=10):
+    h = _create(ipg, g)
+    r1, c1, st = ipg.ipg_pagerank(h, updates, stats_flags=ipg.IPG_STAT_RECEIVERS)
+    r2, _, _ = ipg.ipg_pagerank(h, updates)
+    ref = oracle.pagerank(g.n, g.offsets, g.cols, updates)
+    if g.n:
+        err = np.max(np.abs(r1.astype(np.float64) - ref.values)) / np.max(ref.values)
+        assert err <= PR_TOL, err
+        assert np.array_equal(r1.view(np.uint32), r2.view(np.uint32)), "PageRank is not bit-reproducible"
+    _cmp_stats(st, c1, ref)
+    return r1
+
+
+def check_hashmin(ipg, g):
+    h = _create(ipg, g, directed=False)
+    lab, cnt, st = ipg.ipg_hashmin_cc(h, stats_flags=ipg.IPG_STAT_RECEIVERS)
+    ref = oracle.hashmin(g.n, g.offsets, g.cols)
+    np.testing.assert_array_equal(lab, ref.values)
+    _cmp_stats(st, cnt, ref)
+    return lab
+
+
+def check_sssp(ipg, g, source, weights="graph"):
+    w = g.weights if weights == "graph" else weights
+    h = ipg.ipg_graph_create(g.offsets, g.cols, w, g.n, g.m, g.directed)
+    dist, cnt, st = ipg.ipg_sssp(h, source, stats_flags=ipg.IPG_STAT_RECEIVERS)
+    ref = oracle.sssp(g.n, g.offsets, g.cols, w, source)
+    np.testing.assert_array_equal(dist, ref.values)
+    _cmp_stats(st, cnt, ref)
+    return dist
+
+
+# ---------------------------------------------------------------------------------------
+# adversarial and small graphs
+
+
+def _adversarial(undirected):
+    yield "n1", gen.csr_from_edges(1, [], [], undirected=undirected)
+    yield "isolated", gen.csr_from_edges(7, [], [], undirected=undirected)
+    yield "selfloops", gen.csr_from_edges(4, [0, 1, 1, 3], [0, 1, 1, 3], undirected=undirected)
+    yield "multi", gen.csr_from_edges(6, [0, 0, 0, 2, 3, 3, 5], [1, 1, 1, 3, 4, 4, 5], undirected=undirected)
+    p = 700
+    yield "path", gen.csr_from_edges(p, np.arange(p - 1), np.arange(1, p), undirected=undirected)
+    leaves = 1 << 17  # hub spans many merge-path tiles in both directions
+    yield "hub", gen.csr_from_edges(leaves + 1, np.zeros(leaves, dtype=np.int64), np.arange(1, leaves + 1),
+                                    undirected=undirected)
+    yield "instar", gen.csr_from_edges(300001, np.arange(1, 300001), np.zeros(300000, dtype=np.int64),
+                                       undirected=undirected)
+
+
+@pytest.mark.parametrize("undirected", [False, True])
+def test_pagerank_adversarial(ipg, undirected):
+    for name, g in _adversarial(undirected):
+        check_pagerank(ipg, g)
+
+
+def test_pagerank_closed_forms_on_gpu(ipg):
+    # directed cycle: 1/N everywhere; in-star: closed form for the centre
+    N = 1000
+    g = gen.csr_from_edges(N, np.arange(N), (np.arange(N) + 1) % N)
+    r = check_pagerank(ipg, g)
+    np.testing.assert_allclose(r, 1.0 / N, rtol=1e-6)
+
+
+@pytest.mark.parametrize("updates", [0, 1, 2, 3, 25])
+def test_pagerank_update_counts(ipg, updates):
+    check_pagerank(ipg, gen.rmat(10, 8, seed=4), updates)
+
+
+def test_hashmin_adversarial(ipg):
+    for name, g in _adversarial(True):
+        check_hashmin(ipg, g)
+
+
+def test_sssp_adversarial(ipg):
+    for name, g in _adversarial(False):
+        for src in sorted({0, g.n - 1, g.n // 2}):
+            check_sssp(ipg, g, src, weights=None)
+            w = np.full(g.m, 255, dtype=np.uint32)
+            check_sssp(ipg, g, src, weights=w)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_multigraphs(ipg, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 3000))
+    m = int(rng.integers(0, 25000))
+    g = gen.random_multigraph(n, m, seed=seed, weighted=True)
+    check_pagerank(ipg, g)
+    for src in (0, int(rng.integers(0, n))):
+        check_sssp(ipg, g, src)
+        check_sssp(ipg, g, src, weights=None)
+    u = gen.random_multigraph(n, m // 2, seed=seed, undirected=True)
+    check_hashmin(ipg, u)
+
+
+@pytest.mark.parametrize("scale", [4, 6, 8, 10, 12, 14])
+def test_rmat_scales(ipg, scale):
+    g = gen.rmat(scale, 16, seed=scale, weighted=True)
+    check_pagerank(ipg, g)
+    src = gen.max_out_degree_vertex(g)
+    check_sssp(ipg, g, src)
+    check_sssp(ipg, g, src, weights=None)
+    zero_out = np.nonzero(g.out_degree() == 0)[0]
+    if zero_out.size:
+        check_sssp(ipg, g, int(zero_out[0]))  # a source with no out-edge: one superstep
+    u = gen.rmat(scale, 16, seed=scale, undirected=True)
+    check_hashmin(ipg, u)
+
+
+def test_device_entry_points_match_host(ipg):
+    import torch
+
+    g = gen.rmat(12, 16, seed=9, weighted=True)
+    h = _create(ipg, g)
+    ranks, _, _ = ipg.ipg_pagerank(h, 10)
+    t = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    ipg.ipg_pagerank_dev(h, 10, t)
+    torch.cuda.synchronize()
+    assert np.array_equal(t.cpu().numpy().view(np.uint32), ranks.view(np.uint32))
+    dist, _, _ = ipg.ipg_sssp(h, 0)
+    d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    ipg.ipg_sssp_dev(h, 0, d)
+    np.testing.assert_array_equal(d.cpu().numpy().view(np.uint32), dist)
+    # graph created from device tensors
+    dg = gen.rmat_device(12, 16, seed=9, weighted=True)
+    h2 = ipg.ipg_graph_create_dev(dg.offsets, dg.cols, dg.weights, dg.n, dg.m, True)
+    dist2, _, _ = ipg.ipg_sssp(h2, 0)
+    np.testing.assert_array_equal(dist2, dist)
+    u = gen.rmat(12, 16, seed=9, undirected=True)
+    hu = _create(ipg, u)
+    lab, _, _ = ipg.ipg_hashmin_cc(hu)
+    lt = torch.empty(u.n, dtype=torch.int32, device="cuda")
+    ipg.ipg_hashmin_cc_dev(hu, lt)
+    np.testing.assert_array_equal(lt.cpu().numpy().view(np.uint32), lab)
+
+
+# ---------------------------------------------------------------------------------------
+# errors
+
+
+def test_errors(ipg):
+    good = gen.csr_from_edges(3, [0, 1], [1, 2])
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_graph_create(np.array([0, 2, 1, 2], np.uint64), good.cols, None, 3, 2, True)
+    assert e.value.status == 1
+    with pytest.raises(ipg.IpgError):
+        ipg.ipg_graph_create(np.array([1, 1, 2, 2], np.uint64), good.cols, None, 3, 2, True)
+    with pytest.raises(ipg.IpgError):
+        ipg.ipg_graph_create(good.offsets, np.array([1, 3], np.uint32), None, 3, 2, True)
+    with pytest.raises(ipg.IpgError):
+        ipg.ipg_graph_create(np.array([0, 1, 2, 3], np.uint64), good.cols, None, 3, 2, True)
+    h = _create(ipg, good)
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_hashmin_cc(h)
+    assert e.value.status == 1 and "undirected" in str(e.value)
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_sssp(h, 3)
+    assert e.value.status == 1
+    big = gen.csr_from_edges(3, [0, 1], [1, 2], [0xFFFFFF00, 0xFFFFFF00])
+    hb = _create(ipg, big)
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_sssp(hb, 0)
+    assert e.value.status == 7
+    # the graph stays usable after an error
+    d, c, _ = ipg.ipg_sssp(h, 0)
+    assert list(d) == [0, 1, 2] and c == 4
+
+
+# ---------------------------------------------------------------------------------------
+# the workload configurations at full size
+
+
+def test_config_pagerank_scale16(ipg):
+    """PageRank, 10 supersteps, directed R-MAT scale 16, edge factor 16, seed 1."""
+    g = gen.rmat(16, 16, seed=1)
+    check_pagerank(ipg, g, 10)
+
+
+def test_config_hashmin_scale20(ipg):
+    """Hashmin CC on the undirected R-MAT scale 20, edge factor 16, seed 1."""
+    g = gen.rmat(20, 16, seed=1, undirected=True)
+    check_hashmin(ipg, g)
+
+
+def _rows_chunks(offsets, step):
+    n = offsets.size - 1
+    u = 0
+    while u < n:
+        e0 = int(offsets[u])
+        v = int(np.searchsorted(offsets, e0 + step, side="right")) - 1
+        v = max(v, u + 1)
+        v = min(v, n)
+        yield u, v, e0, int(offsets[v])
+        u = v
+
+
+def test_config_billion_edge(ipg):
+    """R-MAT scale 26, edge factor 28 (1.84e9 edges), weights in [1,255], seed 1:
+    PageRank checked superstep-locally in float64 on sampled vertices plus the mass
+    identity; SSSP from the max-out-degree vertex checked by its full Bellman
+    certificate (every edge relaxed, every reached vertex tight), and its superstep
+    count by the hop-count closed form computed on the tight-edge subgraph."""
+    import torch
+
+    dg = gen.rmat_device(26, 28, seed=1, weighted=True)
+    h = ipg.ipg_graph_create_dev(dg.offsets, dg.cols, dg.weights, dg.n, dg.m, True)
+    g = dg.to_host()
+    del dg
+    torch.cuda.empty_cache()
+    n, m = g.n, g.m
+    assert m > 1_800_000_000
+    outdeg = g.out_degree()
+
+    r9, _, _ = ipg.ipg_pagerank(h, 9)
+    r10, c, st = ipg.ipg_pagerank(h, 10)
+    assert c == 11 and all(s.messages_sent == m for s in st[:10])
+    r9d = r9.astype(np.float64)
+    # mass identity
+    lhs = r10.astype(np.float64).sum()
+    rhs = 0.15 + 0.85 * r9d[outdeg > 0].sum()
+    assert abs(lhs - rhs) <= PR_TOL * rhs
+    # superstep-local check on sampled vertices (in-edges found by scanning all edges)
+    rng = np.random.default_rng(7)
+    sample = np.unique(np.concatenate([np.arange(64), rng.integers(0, n, 4000)]))
+    is_s = np.zeros(n, dtype=bool)
+    is_s[sample] = True
+    acc = np.zeros(n, dtype=np.float64)
+    contrib = np.where(outdeg > 0, r9d / np.maximum(outdeg, 1), 0.0)
+    for u0, u1, e0, e1 in _rows_chunks(g.offsets, 200_000_000):
+        cols = g.cols[e0:e1]
+        hit = np.nonzero(is_s[cols])[0]
+        src = np.searchsorted(g.offsets[u0:u1 + 1].astype(np.int64), hit + e0, side="right") - 1 + u0
+        np.add.at(acc, cols[hit], contrib[src])
+    expect = 0.15 / n + 0.85 * acc[sample]
+    err = np.max(np.abs(r10[sample].astype(np.float64) - expect)) / np.max(r10)
+    assert err <= PR_TOL, err
+
+    src = gen.max_out_degree_vertex(g)
+    dist, cnt, _ = ipg.ipg_sssp(h, src)
+    INF = np.uint64(0xFFFFFFFF)
+    assert dist[src] == 0
+    best = np.full(n, np.iinfo(np.uint64).max, dtype=np.uint64)
+    d64 = dist.astype(np.uint64)
+    tight_src, tight_dst = [], []
+    for u0, u1, e0, e1 in _rows_chunks(g.offsets, 200_000_000):
+        rows = np.repeat(np.arange(u0, u1, dtype=np.int64), outdeg[u0:u1])
+        du = d64[rows]
+        ok = du != INF
+        cand = du[ok] + g.weights[e0:e1][ok].astype(np.uint64)
+        cols = g.cols[e0:e1][ok]
+        assert (d64[cols] <= cand).all(), "an edge is not relaxed"
+        np.minimum.at(best, cols, cand)
+        t = d64[cols] == cand
+        tight_src.append(rows[ok][t])
+        tight_dst.append(cols[t])
+    reached = d64 != INF
+    reached[src] = False
+    np.testing.assert_array_equal(best[reached], d64[reached])
+    assert (best[(d64 == INF)] == np.iinfo(np.uint64).max).all()
+    # hop count of the fewest-hop shortest path, by relaxing over the tight edges
+    ts, td = np.concatenate(tight_src), np.concatenate(tight_dst)
+    hops = np.full(n, np.iinfo(np.int64).max, dtype=np.int64)
+    hops[src] = 0
+    for _ in range(10_000):
+        cand = np.full(n, np.iinfo(np.int64).max, dtype=np.int64)
+        fin = hops[ts] != np.iinfo(np.int64).max
+        np.minimum.at(cand, td[fin], hops[ts[fin]] + 1)
+        new = np.minimum(hops, cand)
+        if np.array_equal(new, hops):
+            break
+        hops = new
+    senders = (d64 != INF) & (outdeg > 0)
+    assert cnt == 2 + int(hops[senders].max())
