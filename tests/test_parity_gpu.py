@@ -65,8 +65,11 @@ def check_hashmin(ipg, g):
     return lab
 
 
-def check_sssp(ipg, g, source, weights="graph"):
-    w = g.weights if weights == "graph" else weights
+_GRAPH_WEIGHTS = object()
+
+
+def check_sssp(ipg, g, source, weights=_GRAPH_WEIGHTS):
+    w = g.weights if weights is _GRAPH_WEIGHTS else weights
     h = ipg.ipg_graph_create(g.offsets, g.cols, w, g.n, g.m, g.directed)
     dist, cnt, st = ipg.ipg_sssp(h, source, stats_flags=ipg.IPG_STAT_RECEIVERS)
     ref = oracle.sssp(g.n, g.offsets, g.cols, w, source)
@@ -209,7 +212,7 @@ def test_errors(ipg):
     assert e.value.status == 7
     # the graph stays usable after an error
     d, c, _ = ipg.ipg_sssp(h, 0)
-    assert list(d) == [0, 1, 2] and c == 4
+    assert list(d) == [0, 1, 2] and c == 3  # 2 + hops to vertex 1, the last sender
 
 
 # ---------------------------------------------------------------------------------------
