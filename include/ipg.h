@@ -145,6 +145,33 @@ ipg_status ipg_hashmin_cc_dev(ipg_graph* g, uint32_t* labels_dev, ipg_stats* sta
 ipg_status ipg_sssp(ipg_graph* g, uint32_t source, uint32_t* dist_out, ipg_stats* stats);
 ipg_status ipg_sssp_dev(ipg_graph* g, uint32_t source, uint32_t* dist_dev, ipg_stats* stats, void* stream);
 
+/*
+ * ipg_sssp_noalloc — the same SSSP as ipg_sssp, for callers that may not
+ * allocate device memory (the paper has no counterpart to this call).
+ * Callers whose device memory belongs to another allocator (a framework's
+ * pool, a budget fixed at start-up) or that run on a latency-critical path
+ * cannot afford cudaMalloc/cudaFree, which can fail and stall the device; they
+ * cannot create an ipg_graph, since that copies the graph and allocates.  This
+ * call reads the caller's device CSR in place and allocates nothing: its working
+ * state lives in one fixed scratch array inside the library's device image,
+ * 16 MiB on every GPU that loads the library, held until the process exits.
+ *   offsets_dev, columns_dev, weights_dev (or NULL), n, m: a device CSR on the
+ *       current device, as for ipg_graph_create; it is validated on every call;
+ *   n <= IPG_NOALLOC_MAX_VERTICES, else IPG_EINVAL;  source < n;
+ *   dist_dev: device, n uint32 (UINT32_MAX = unreachable), caller-owned;
+ *   supersteps_out: optional, the Pregel superstep count;
+ *   stream: cudaStream_t as void* (NULL = legacy default stream).
+ * The first call on a device looks up the scratch array's device address (with
+ * that device current); make that first call before any stream capture.  Every
+ * call on a device shares the one scratch array and finds the previous call's
+ * contents there (it clears what must start at zero): calls that overlap on the
+ * GPU, from several streams or threads, race and give wrong results.
+ */
+#define IPG_NOALLOC_MAX_VERTICES (1u << 20)
+ipg_status ipg_sssp_noalloc(const uint64_t* offsets_dev, const uint32_t* columns_dev, const uint32_t* weights_dev,
+                            uint32_t n, uint64_t m, uint32_t source, uint32_t* dist_dev, uint32_t* supersteps_out,
+                            void* stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char* ipg_last_error(void);
 

@@ -285,3 +285,23 @@ def ipg_sssp_dev(g: Graph, source: int, dist_dev, stats_flags: int = 0, stats_ca
     n = ipg_graph_info(g)["n"]
     return _run_dev(load_library().ipg_sssp_dev, (g.handle, source, _dev_ptr(dist_dev, 4, n, "dist")),
                     stats_flags, stats_cap, stream)
+
+
+def ipg_sssp_noalloc(offsets, columns, weights, n: int, m: int, source: int, dist_dev, stream=None) -> int:
+    """SSSP on a caller-owned device CSR (torch CUDA tensors) into ``dist_dev``, with no
+    device allocation by the library (fixed scratch, n <= IPG_NOALLOC_MAX_VERTICES).
+    Returns the superstep count."""
+    lib = load_library()
+    fn = lib.ipg_sssp_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                   ctypes.c_uint32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    steps = ctypes.c_uint32()
+    _check(fn(_dev_ptr(offsets, 8, n + 1, "offsets"), _dev_ptr(columns, 4, m, "columns"),
+              _dev_ptr(weights, 4, m, "weights"), n, m, source, _dev_ptr(dist_dev, 4, n, "dist"),
+              ctypes.byref(steps), _stream_ptr(stream)))
+    return int(steps.value)
+
+
+IPG_NOALLOC_MAX_VERTICES = 1 << 20
+__all__ += ["ipg_sssp_noalloc", "IPG_NOALLOC_MAX_VERTICES"]
