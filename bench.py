@@ -203,22 +203,22 @@ def kernel_hash(files):
     return h.hexdigest()[:16]
 
 
-PR_KERNEL_FILES = ["paper_2010_01542_gb300/csrc/ipg_pagerank.cu", "paper_2010_01542_gb300/csrc/ipg_internal.cuh"]
+KERNEL_FILES = {
+    "pr_pull_kernel": ["paper_2010_01542_gb300/csrc/ipg_pagerank.cu", "paper_2010_01542_gb300/csrc/ipg_internal.cuh"],
+    "push_relax_kernel": ["paper_2010_01542_gb300/csrc/ipg_push.cu", "paper_2010_01542_gb300/csrc/ipg_internal.cuh"],
+}
 
 
-def measured_traffic(kernel, n, m):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu record (profiles/traffic.json), if it
+    was taken on this workload and on the current kernel source; else None."""
     try:
-        d = json.load(open(path))[kernel]
+        d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
     except Exception:
         return None
-    if d.get("source_hash") != kernel_hash(PR_KERNEL_FILES):
+    if d.get("source_hash") != kernel_hash(KERNEL_FILES[kernel]) or d.get("workload") != workload:
         return None
-    # captured on a smaller graph of the same family: scale by algorithmic units
-    units = 8 * m + 24 * n
-    return d["dram_bytes_per_launch"] * units / d["algorithmic_bytes_per_launch"]
+    return d["dram_bytes_per_launch"]
 
 
 def peak_hbm():
@@ -287,16 +287,34 @@ def run_ours(a):
     launches_per_step = (1 + 2 * PR_UPDATES) + statistics.mean(
         1 + 5 * sum(1 for s in sst if s.senders > 0) for _, sst in all_stats)
 
-    # roofline: the PageRank pull kernel (the dominant kernel of the step)
-    alg_bytes = 8 * m + 24 * n
-    pr_mean = statistics.mean(pr_kernel_ms)
-    achieved = alg_bytes / (pr_mean / 1e3) / 1e9
+    # roofline for the kernel that dominates the step (by CUDA-event time in the timed region)
     peak, peak_kind = peak_hbm()
-    traffic = measured_traffic("pr_pull_kernel", n, m)
-    roofline = {"bound": "hbm", "kernel": "pr_pull_kernel", "achieved": round(achieved, 1), "peak": peak,
-                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None if traffic is None else int(traffic),
-                "algorithmic_bytes": alg_bytes, "kernel_ms": round(pr_mean, 4)}
+    wl = f"rmat{a.scale}-ef{a.edge_factor}"
+    pr_bytes = 8 * m + 24 * n  # per pull superstep
+    pr_total_ms = sum(pr_kernel_ms)
+    sssp_launch_bytes = [12 * s.messages_sent + 16 * s.senders for _, sst in all_stats for s in sst if s.senders]
+    sssp_launch_ms = [s.kernel_ms for _, sst in all_stats for s in sst if s.senders]
+    kernels = {
+        "pr_pull_kernel": {"launches": len(pr_kernel_ms), "total_ms": round(pr_total_ms, 3),
+                           "algorithmic_bytes_per_launch": pr_bytes,
+                           "achieved_gbs": round(pr_bytes * len(pr_kernel_ms) / (pr_total_ms / 1e3) / 1e9, 1),
+                           "traffic_per_launch": measured_traffic("pr_pull_kernel", wl),
+                           "bytes_rule": "8 m + 24 n per launch"},
+        "push_relax_kernel": {"launches": len(sssp_launch_ms), "total_ms": round(sum(sssp_launch_ms), 3),
+                              "algorithmic_bytes_per_launch": int(statistics.mean(sssp_launch_bytes)),
+                              "achieved_gbs": round(sum(sssp_launch_bytes) / (sum(sssp_launch_ms) / 1e3) / 1e9, 1),
+                              "traffic_per_launch": measured_traffic("push_relax_kernel", wl),
+                              "bytes_rule": "12 B per message + 16 B per frontier vertex"},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    kd = kernels[dom]
+    share = kd["total_ms"] / sum(k["total_ms"] for k in kernels.values())
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kd["achieved_gbs"], "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(kd["achieved_gbs"] / peak, 4),
+                "traffic": None if kd["traffic_per_launch"] is None else int(kd["traffic_per_launch"]),
+                "algorithmic_bytes_per_launch": kd["algorithmic_bytes_per_launch"],
+                "share_of_kernel_time": round(share, 3)}
+    pr_mean = statistics.mean(pr_kernel_ms)
 
     # end to end through the host-buffer C ABI
     e2e = None
@@ -339,12 +357,13 @@ def run_ours(a):
                        "sssp_source": src, "l2": "inputs larger than L2 (graph %.1f GB resident)" %
                        ((host.offsets.nbytes + 2 * host.cols.nbytes) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * a.steps)), "clocks": clocks,
             "pagerank": {"edges_per_step": pr_edges, "ms_per_superstep": round(statistics.mean(pr_step_ms), 4),
                          "kernel_ms": round(pr_mean, 4),
                          "gteps": round(m / (statistics.mean(pr_step_ms) / 1e3) / 1e9, 2)},
             "sssp": {"edges_per_step": int(statistics.mean(sssp_edges)), "supersteps": sssp_supersteps[0],
+                     "messages_per_superstep": [s.messages_sent for s in all_stats[-1][1]],
                      "ms": round(statistics.mean(sssp_ms), 3), "kernel_ms": round(statistics.mean(sssp_kernel_ms), 3),
                      "gteps": round(statistics.mean(sssp_edges) / (statistics.mean(sssp_ms) / 1e3) / 1e9, 2)},
         }
