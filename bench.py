@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--pull-divisor", type=int, default=None,
+                   help="Hashmin/SSSP direction knob (library default if omitted; 0 = always push)")
     return p.parse_args()
 
 
@@ -240,6 +242,8 @@ def run_ours(a):
 
     world, rank, local = dist_init(a)
     ipg.load_library()
+    if a.pull_divisor is not None:
+        ipg.ipg_set_tuning("pull_divisor", a.pull_divisor)
     dg = gen.rmat_device(a.scale, a.edge_factor, seed=a.seed, weighted=True, device=local)
     n, m = dg.n, dg.m
     stream = torch.cuda.Stream()
@@ -363,6 +367,8 @@ def run_ours(a):
                          "kernel_ms": round(pr_mean, 4),
                          "gteps": round(m / (statistics.mean(pr_step_ms) / 1e3) / 1e9, 2)},
             "sssp": {"edges_per_step": int(statistics.mean(sssp_edges)), "supersteps": sssp_supersteps[0],
+                     "pull_divisor": ipg.ipg_get_tuning("pull_divisor"),
+                     "kernel_ms_per_superstep": [round(s.kernel_ms, 3) for s in all_stats[-1][1]],
                      "messages_per_superstep": [s.messages_sent for s in all_stats[-1][1]],
                      "ms": round(statistics.mean(sssp_ms), 3), "kernel_ms": round(statistics.mean(sssp_kernel_ms), 3),
                      "gteps": round(statistics.mean(sssp_edges) / (statistics.mean(sssp_ms) / 1e3) / 1e9, 2)},

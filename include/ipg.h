@@ -172,6 +172,19 @@ ipg_status ipg_sssp_noalloc(const uint64_t* offsets_dev, const uint32_t* columns
                             uint32_t n, uint64_t m, uint32_t source, uint32_t* dist_dev, uint32_t* supersteps_out,
                             void* stream);
 
+/*
+ * Process-wide tuning knobs (not in the paper; they change speed, never results):
+ *   "pull_divisor"  Hashmin/SSSP superstep direction.  A superstep whose messages
+ *                   (sum of the senders' out-degrees) reach m / pull_divisor runs in
+ *                   pull form (every vertex scans its in-edges, as the paper's
+ *                   pull-based CC version does, Sec. VI-C) instead of push form.
+ *                   0 = always push.  Default 6.
+ * Unknown names or invalid values return IPG_EINVAL.  Set knobs between calls,
+ * not while a call runs.
+ */
+ipg_status ipg_set_tuning(const char* name, int64_t value);
+ipg_status ipg_get_tuning(const char* name, int64_t* value);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char* ipg_last_error(void);
 

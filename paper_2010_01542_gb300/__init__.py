@@ -305,3 +305,23 @@ def ipg_sssp_noalloc(offsets, columns, weights, n: int, m: int, source: int, dis
 
 IPG_NOALLOC_MAX_VERTICES = 1 << 20
 __all__ += ["ipg_sssp_noalloc", "IPG_NOALLOC_MAX_VERTICES"]
+
+
+def ipg_set_tuning(name: str, value: int) -> None:
+    """Set a process-wide tuning knob (see include/ipg.h); speed only, never results."""
+    lib = load_library()
+    lib.ipg_set_tuning.argtypes = [ctypes.c_char_p, ctypes.c_int64]
+    lib.ipg_set_tuning.restype = ctypes.c_int
+    _check(lib.ipg_set_tuning(name.encode(), int(value)))
+
+
+def ipg_get_tuning(name: str) -> int:
+    lib = load_library()
+    lib.ipg_get_tuning.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64)]
+    lib.ipg_get_tuning.restype = ctypes.c_int
+    v = ctypes.c_int64()
+    _check(lib.ipg_get_tuning(name.encode(), ctypes.byref(v)))
+    return int(v.value)
+
+
+__all__ += ["ipg_set_tuning", "ipg_get_tuning"]

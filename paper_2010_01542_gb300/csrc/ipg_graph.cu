@@ -8,6 +8,7 @@
 #include <cub/device/device_scan.cuh>
 
 #include "ipg_internal.cuh"
+#include "ipg_mergepath.cuh"
 
 namespace ipg {
 
@@ -113,6 +114,24 @@ __global__ void expand_sources_kernel(const uint64_t* __restrict__ off, uint32_t
     }
 }
 
+__global__ void csc_gather_kernel(const uint32_t* __restrict__ idx, uint64_t m, const uint32_t* __restrict__ src_of,
+                                  const uint8_t* __restrict__ w8, const uint32_t* __restrict__ w32,
+                                  uint32_t* __restrict__ csc_src, uint8_t* __restrict__ csc_w8,
+                                  uint32_t* __restrict__ csc_w32) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const uint32_t e = idx[i];
+        csc_src[i] = src_of[e];
+        if (csc_w8) csc_w8[i] = w8[e];
+        if (csc_w32) csc_w32[i] = w32[e];
+    }
+}
+
+__global__ void iota_kernel(uint32_t* __restrict__ a, uint64_t m) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) a[i] = (uint32_t)i;
+}
+
 __global__ void count_in_degree_kernel(const uint32_t* __restrict__ col, uint64_t m,
                                        unsigned long long* __restrict__ indeg) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -133,16 +152,21 @@ ipg_status ensure_csc(ipg_graph* g, cudaStream_t st) {
     if (!g->directed) {
         g->csc_off = g->off;
         g->csc_src = g->col;
+        g->csc_w8 = g->w8;
+        g->csc_w = g->w;
         g->csc_owned = false;
         g->csc_ready = true;
         return IPG_OK;
     }
+    const bool weighted = g->w8 || g->w;
     const uint32_t n = g->n;
     const uint64_t m = g->m;
     const int sms = device_sms(g->device);
     unsigned long long* indeg = nullptr;
     uint32_t* src_in = nullptr;
     uint32_t* keys_out = nullptr;
+    uint32_t* idx_in = nullptr;
+    uint32_t* idx_out = nullptr;
     void* temp = nullptr;
     size_t temp_bytes = 0, scan_bytes = 0;
     ipg_status rc = IPG_OK;
@@ -158,6 +182,8 @@ ipg_status ensure_csc(ipg_graph* g, cudaStream_t st) {
     {
         CSC_CUDA(cudaMalloc(&g->csc_off, sizeof(uint64_t) * ((size_t)n + 1)));
         CSC_CUDA(cudaMalloc(&g->csc_src, sizeof(uint32_t) * (m ? m : 1)));
+        if (g->w8) CSC_CUDA(cudaMalloc(&g->csc_w8, m ? m : 1));
+        if (g->w) CSC_CUDA(cudaMalloc(&g->csc_w, sizeof(uint32_t) * (m ? m : 1)));
         g->csc_owned = true;
         CSC_CUDA(cudaMalloc(&indeg, sizeof(unsigned long long) * ((size_t)n + 1)));
         CSC_CUDA(cudaMemsetAsync(indeg, 0, sizeof(unsigned long long) * ((size_t)n + 1), st));
@@ -186,9 +212,23 @@ ipg_status ensure_csc(ipg_graph* g, cudaStream_t st) {
             int bits = 1;
             while (bits < 32 && (1ull << bits) < (uint64_t)n) ++bits;
             size_t tb = temp_bytes;
-            CSC_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, (const uint32_t*)g->col, keys_out,
-                                                     (const uint32_t*)src_in, g->csc_src, (long long)m, 0, bits,
-                                                     st));
+            if (!weighted) {
+                CSC_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, (const uint32_t*)g->col, keys_out,
+                                                         (const uint32_t*)src_in, g->csc_src, (long long)m, 0, bits,
+                                                         st));
+            } else {
+                // sort edge indices by destination (stable), then gather sources and weights
+                CSC_CUDA(cudaMalloc(&idx_in, sizeof(uint32_t) * m));
+                CSC_CUDA(cudaMalloc(&idx_out, sizeof(uint32_t) * m));
+                iota_kernel<<<grid_for(m, sms, 16), 256, 0, st>>>(idx_in, m);
+                CSC_CUDA(cudaGetLastError());
+                CSC_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, (const uint32_t*)g->col, keys_out,
+                                                         (const uint32_t*)idx_in, idx_out, (long long)m, 0, bits,
+                                                         st));
+                csc_gather_kernel<<<grid_for(m, sms, 16), 256, 0, st>>>(idx_out, m, src_in, g->w8, g->w, g->csc_src,
+                                                                        g->csc_w8, g->csc_w);
+                CSC_CUDA(cudaGetLastError());
+            }
         }
         CSC_CUDA(cudaStreamSynchronize(st));
         g->csc_ready = true;
@@ -198,12 +238,18 @@ done:
     if (indeg) cudaFree(indeg);
     if (src_in) cudaFree(src_in);
     if (keys_out) cudaFree(keys_out);
+    if (idx_in) cudaFree(idx_in);
+    if (idx_out) cudaFree(idx_out);
     if (temp) cudaFree(temp);
     if (rc != IPG_OK) {
         if (g->csc_off) cudaFree(g->csc_off);
         if (g->csc_src) cudaFree(g->csc_src);
+        if (g->csc_w8) cudaFree(g->csc_w8);
+        if (g->csc_w) cudaFree(g->csc_w);
         g->csc_off = nullptr;
         g->csc_src = nullptr;
+        g->csc_w8 = nullptr;
+        g->csc_w = nullptr;
         g->csc_owned = false;
     }
     return rc;
@@ -225,6 +271,181 @@ ipg_status count_in_nonempty(ipg_graph* g, cudaStream_t st) {
     return IPG_OK;
 }
 
+ipg_status ensure_pull_partition(ipg_graph* g, cudaStream_t st) {
+    if (g->pr_tile_row) return IPG_OK;
+    IPG_TRY(ensure_csc(g, st));
+    const uint64_t tiles = mp_tile_count(g->n, g->m);
+    IPG_CUDA(cudaMalloc(&g->pr_tile_row, sizeof(uint32_t) * (tiles + 1)));
+    IPG_CUDA(cudaMalloc(&g->pr_head, sizeof(float) * (tiles ? tiles : 1)));
+    IPG_CUDA(cudaMalloc(&g->pr_tail, sizeof(float) * (tiles ? tiles : 1)));
+    IPG_TRY(mp_partition(g->csc_off, g->n, g->m, tiles, g->pr_tile_row, st));
+    g->pr_tiles = tiles;
+    return IPG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Degree-ordered relabelling (done once, when the graph is created).  Random
+// accesses in every superstep land on the values of hub vertices; numbering the
+// vertices by decreasing total degree packs those values into few cache lines and
+// keeps them in L2.  The permutation is invisible to callers: sources are mapped
+// in, outputs are mapped back, and Hashmin labels stay the caller's ids.
+
+__global__ void degree_key_kernel(const uint64_t* __restrict__ off, const unsigned long long* __restrict__ indeg,
+                                  uint32_t n, uint32_t* __restrict__ key, uint32_t* __restrict__ ids) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        unsigned long long d = (off[v + 1] - off[v]) + (indeg ? indeg[v] : 0ull);
+        key[v] = ~(uint32_t)(d < 0xFFFFFFFFull ? d : 0xFFFFFFFFull);  // ascending sort = descending degree
+        ids[v] = (uint32_t)v;
+    }
+}
+
+__global__ void invert_kernel(const uint32_t* __restrict__ perm, uint32_t n, uint32_t* __restrict__ inv,
+                              const uint64_t* __restrict__ off, unsigned long long* __restrict__ new_deg) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        const uint32_t o = perm[x];
+        inv[o] = (uint32_t)x;
+        new_deg[x] = off[o + 1] - off[o];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) new_deg[n] = 0;
+}
+
+__global__ void max_weight_kernel(const uint32_t* __restrict__ w, uint64_t m, unsigned int* out) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    unsigned mx = 0;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) mx = max(mx, w[e]);
+    for (int s = 16; s > 0; s >>= 1) mx = max(mx, __shfl_down_sync(0xFFFFFFFFu, mx, s));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+// one warp per new row: copy the old row, renaming its columns
+__global__ void rename_rows_kernel(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col,
+                                   const uint32_t* __restrict__ w, const uint32_t* __restrict__ perm,
+                                   const uint32_t* __restrict__ inv, const uint64_t* __restrict__ new_off, uint32_t n,
+                                   uint32_t* __restrict__ new_col, uint32_t* __restrict__ new_w,
+                                   uint8_t* __restrict__ new_w8) {
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t x = warp; x < n; x += nwarps) {
+        const uint32_t o = perm[x];
+        const uint64_t b = off[o], len = off[o + 1] - b, nb = new_off[x];
+        for (uint64_t k = lane; k < len; k += 32) {
+            new_col[nb + k] = inv[col[b + k]];
+            if (new_w) new_w[nb + k] = w[b + k];
+            if (new_w8) new_w8[nb + k] = (uint8_t)w[b + k];
+        }
+    }
+}
+
+static ipg_status relabel(ipg_graph* g, cudaStream_t st) {
+    const uint32_t n = g->n;
+    const uint64_t m = g->m;
+    if (n == 0) return IPG_OK;
+    const int sms = device_sms(g->device);
+    unsigned long long* indeg = nullptr;
+    unsigned long long* new_deg = nullptr;
+    uint32_t *key = nullptr, *key_out = nullptr, *ids = nullptr;
+    uint64_t* new_off = nullptr;
+    uint32_t* new_col = nullptr;
+    uint32_t* new_w = nullptr;
+    uint8_t* new_w8 = nullptr;
+    void* temp = nullptr;
+    size_t tb = 0, tb2 = 0;
+    ipg_status rc = IPG_OK;
+    cudaError_t e;
+    unsigned wmax = 0;
+#define RL(call)                                          \
+    do {                                                  \
+        e = (call);                                       \
+        if (e != cudaSuccess) {                           \
+            rc = cuda_fail(e, #call, __FILE__, __LINE__); \
+            goto done;                                    \
+        }                                                 \
+    } while (0)
+    RL(cudaMalloc(&g->perm, sizeof(uint32_t) * n));
+    RL(cudaMalloc(&g->inv, sizeof(uint32_t) * n));
+    RL(cudaMalloc(&key, sizeof(uint32_t) * n));
+    RL(cudaMalloc(&key_out, sizeof(uint32_t) * n));
+    RL(cudaMalloc(&ids, sizeof(uint32_t) * n));
+    RL(cudaMalloc(&new_deg, sizeof(unsigned long long) * ((size_t)n + 1)));
+    RL(cudaMalloc(&new_off, sizeof(uint64_t) * ((size_t)n + 1)));
+    if (g->directed && m) {
+        RL(cudaMalloc(&indeg, sizeof(unsigned long long) * ((size_t)n + 1)));
+        RL(cudaMemsetAsync(indeg, 0, sizeof(unsigned long long) * ((size_t)n + 1), st));
+        count_in_degree_kernel<<<grid_for(m, sms, 16), 256, 0, st>>>(g->col, m, indeg);
+        RL(cudaGetLastError());
+    }
+    degree_key_kernel<<<grid_for(n, sms), 256, 0, st>>>(g->off, indeg, n, key, ids);
+    RL(cudaGetLastError());
+    RL(cub::DeviceRadixSort::SortPairs(nullptr, tb, (const uint32_t*)key, key_out, (const uint32_t*)ids, g->perm,
+                                       (long long)n, 0, 32, st));
+    RL(cub::DeviceScan::ExclusiveSum(nullptr, tb2, new_deg, (unsigned long long*)new_off, (long long)n + 1, st));
+    if (tb2 > tb) tb = tb2;
+    RL(cudaMalloc(&temp, tb ? tb : 16));
+    tb2 = tb;
+    RL(cub::DeviceRadixSort::SortPairs(temp, tb2, (const uint32_t*)key, key_out, (const uint32_t*)ids, g->perm,
+                                       (long long)n, 0, 32, st));
+    invert_kernel<<<grid_for(n, sms), 256, 0, st>>>(g->perm, n, g->inv, g->off, new_deg);
+    RL(cudaGetLastError());
+    tb2 = tb;
+    RL(cub::DeviceScan::ExclusiveSum(temp, tb2, new_deg, (unsigned long long*)new_off, (long long)n + 1, st));
+    if (g->w && m) {
+        RL(cudaMemsetAsync(&g->counters->status, 0, sizeof(unsigned), st));
+        max_weight_kernel<<<grid_for(m, sms, 16), 256, 0, st>>>(g->w, m, &g->counters->status);
+        RL(cudaGetLastError());
+        RL(cudaMemcpyAsync(&g->h_counters->status, &g->counters->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        RL(cudaStreamSynchronize(st));
+        wmax = g->h_counters->status;
+        RL(cudaMemsetAsync(&g->counters->status, 0, sizeof(unsigned), st));
+    }
+    RL(cudaMalloc(&new_col, sizeof(uint32_t) * (m ? m : 1)));
+    if (g->w) {
+        if (wmax <= 255)
+            RL(cudaMalloc(&new_w8, m ? m : 1));
+        else
+            RL(cudaMalloc(&new_w, sizeof(uint32_t) * (m ? m : 1)));
+    }
+    if (m) {
+        rename_rows_kernel<<<grid_for((uint64_t)n * 32, sms, 16), 256, 0, st>>>(g->off, g->col, g->w, g->perm, g->inv,
+                                                                                new_off, n, new_col, new_w, new_w8);
+        RL(cudaGetLastError());
+    }
+    RL(cudaStreamSynchronize(st));
+    cudaFree(g->off);
+    cudaFree(g->col);
+    if (g->w) cudaFree(g->w);
+    g->off = new_off;
+    g->col = new_col;
+    g->w = new_w;
+    g->w8 = new_w8;
+    new_off = nullptr;
+    new_col = nullptr;
+    new_w = nullptr;
+    new_w8 = nullptr;
+done:
+#undef RL
+    if (indeg) cudaFree(indeg);
+    if (new_deg) cudaFree(new_deg);
+    if (key) cudaFree(key);
+    if (key_out) cudaFree(key_out);
+    if (ids) cudaFree(ids);
+    if (temp) cudaFree(temp);
+    if (new_off) cudaFree(new_off);
+    if (new_col) cudaFree(new_col);
+    if (new_w) cudaFree(new_w);
+    if (new_w8) cudaFree(new_w8);
+    return rc;
+}
+
+int sm_count_of(int dev) { return device_sms(dev); }
+
+Tuning& tuning() {
+    static Tuning t;
+    return t;
+}
+
 // ---------------------------------------------------------------------------
 // creation
 
@@ -237,10 +458,18 @@ static void free_graph(ipg_graph* g) {
     if (g->csc_owned) {
         f(g->csc_off);
         f(g->csc_src);
+        f(g->csc_w8);
+        f(g->csc_w);
     }
     f(g->off);
     f(g->col);
     f(g->w);
+    f(g->w8);
+    f(g->perm);
+    f(g->inv);
+    f(g->val);
+    f(g->sval);
+    f(g->pr_rank);
     f(g->inv_outdeg);
     f(g->pr_box[0]);
     f(g->pr_box[1]);
@@ -322,9 +551,13 @@ static ipg_status create_impl(const uint64_t* offsets, const uint32_t* columns, 
             rc = set_error(IPG_EINVAL, "ipg_graph_create: a column index is >= n");
             break;
         }
+        rc = relabel(g, st);
+        if (rc != IPG_OK) break;
         if (!g->directed) {
             g->csc_off = g->off;
             g->csc_src = g->col;
+            g->csc_w8 = g->w8;
+            g->csc_w = g->w;
             g->csc_ready = true;
         }
     } while (0);
@@ -380,5 +613,24 @@ const char* ipg_status_string(ipg_status s) {
 }
 
 int ipg_version(void) { return 100; }
+
+ipg_status ipg_set_tuning(const char* name, int64_t value) {
+    if (!name) return set_error(IPG_EINVAL, "ipg_set_tuning: name is NULL");
+    if (!strcmp(name, "pull_divisor")) {
+        if (value < 0) return set_error(IPG_EINVAL, "ipg_set_tuning: pull_divisor must be >= 0");
+        tuning().pull_divisor = value;
+        return IPG_OK;
+    }
+    return set_error(IPG_EINVAL, "ipg_set_tuning: unknown knob '%s'", name);
+}
+
+ipg_status ipg_get_tuning(const char* name, int64_t* value) {
+    if (!name || !value) return set_error(IPG_EINVAL, "ipg_get_tuning: NULL argument");
+    if (!strcmp(name, "pull_divisor")) {
+        *value = tuning().pull_divisor;
+        return IPG_OK;
+    }
+    return set_error(IPG_EINVAL, "ipg_get_tuning: unknown knob '%s'", name);
+}
 
 }  // extern "C"

@@ -79,14 +79,21 @@ struct ipg_graph {
     int directed = 1;
     int weighted = 0;
 
-    // CSR (out-edges)
+    // CSR (out-edges) in the library's internal vertex numbering: vertices are
+    // relabelled by decreasing total degree when the graph is created, so the
+    // most-accessed values sit together; perm/inv translate at the boundary.
     uint64_t* off = nullptr;
     uint32_t* col = nullptr;
-    uint32_t* w = nullptr;
+    uint32_t* w = nullptr;       // u32 weights (only when some weight exceeds 255)
+    uint8_t* w8 = nullptr;       // u8 weights (when every weight fits in a byte)
+    uint32_t* perm = nullptr;    // internal id -> caller's id
+    uint32_t* inv = nullptr;     // caller's id -> internal id
 
     // CSC (in-edges) for pull; aliases the CSR on undirected graphs
     uint64_t* csc_off = nullptr;
     uint32_t* csc_src = nullptr;
+    uint8_t* csc_w8 = nullptr;    // in-edge weights, same kind as the CSR's
+    uint32_t* csc_w = nullptr;
     bool csc_ready = false;
     bool csc_owned = false;
     long long in_nonempty = -1;  // vertices with in-degree > 0 (PageRank receivers), lazily counted
@@ -95,8 +102,9 @@ struct ipg_graph {
     float* inv_outdeg = nullptr;
     float* pr_box[2] = {nullptr, nullptr};  // outbox double buffer
     uint32_t* pr_tile_row = nullptr;        // merge-path tile boundaries over the CSC
-    float* pr_head = nullptr;               // per tile: partial sum of the row that began in an earlier tile
-    float* pr_tail = nullptr;               // per tile: partial sum of the row that continues past it
+    float* pr_head = nullptr;               // per tile: partial of the row that began in an earlier tile
+    float* pr_tail = nullptr;               // per tile: partial of the row that continues past it
+                                            // (4-byte slots, also used as u32 by pull-min supersteps)
     uint64_t pr_tiles = 0;
     float* pr_out_stage = nullptr;          // host-variant output staging
     size_t pr_out_stage_cap = 0;
@@ -113,6 +121,9 @@ struct ipg_graph {
     uint32_t* push_tile_row = nullptr;
     size_t push_tile_cap = 0;
     uint32_t* val_stage = nullptr;            // host-variant value buffer
+    uint32_t* val = nullptr;                  // values in internal numbering
+    float* pr_rank = nullptr;                 // final ranks in internal numbering
+    uint32_t* sval = nullptr;                 // pull supersteps: value sent by each vertex, kInf if none
     ipg::PushCounters* counters = nullptr;    // device
     ipg::PushCounters* h_counters = nullptr;  // pinned host mirror
 
@@ -123,8 +134,18 @@ struct ipg_graph {
 namespace ipg {
 // in ipg_graph.cu
 ipg_status ensure_csc(ipg_graph* g, cudaStream_t st);
+ipg_status ensure_pull_partition(ipg_graph* g, cudaStream_t st);
 ipg_status count_in_nonempty(ipg_graph* g, cudaStream_t st);
 ipg_status ensure_push_workspace(ipg_graph* g, bool receivers);
+int sm_count_of(int dev);
+// in ipg_pull_min.cu
+ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, const uint32_t* F, const uint32_t* fval, uint32_t f,
+                              uint32_t* val, uint32_t* next, cudaStream_t st, cudaEvent_t ev_kernel);
+// process-wide tuning knobs (ipg_set_tuning)
+struct Tuning {
+    long long pull_divisor = 6;  // pull when a superstep's messages reach m / pull_divisor; 0 = never
+};
+Tuning& tuning();
 // stats helpers
 void stats_begin(ipg_stats* s);
 void stats_put(ipg_stats* s, uint32_t idx, const ipg_superstep_stats& rec);

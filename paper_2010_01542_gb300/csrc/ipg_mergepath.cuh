@@ -1,0 +1,196 @@
+// Merge-path tile engine for pull supersteps (in-edge reductions).
+//
+// The in-edge lists (CSC) are cut into tiles of kMpTile items along the merge
+// path of row ends and edges (Merrill & Garland's merge-based split): every tile
+// holds the same number of (rows + edges), so a vertex with a million in-edges is
+// spread over many CTAs and a run of vertices without in-edges costs one item
+// each — the paper's edge-centric workload proxy (Sec. V-A) made exact.
+//
+// One tile is processed by a CTA as:
+//   1. stage   the tile's row ends (relative, clamped) and each edge's message
+//              (a caller-supplied gather) into shared memory;
+//   2. walk    each thread takes kItems consecutive merge items, sums (or mins)
+//              the messages of every row that starts and ends in its slice and
+//              keeps the partial of its first and last row;
+//   3. scan    a segmented scan of the per-thread carries, in a fixed tree order,
+//              gives each thread the carry-in for its first finished row;
+//   4. emit    every row whose in-edges began in this tile is handed to the
+//              caller's emit functor; a row that began in an earlier tile leaves
+//              its partial in tile_head and is finished by the fix-up kernel,
+//              which folds the tiles' partials in tile order.
+// With a fixed combine order in every step, float sums are bit-reproducible.
+#pragma once
+
+#include "ipg_internal.cuh"
+
+namespace ipg {
+
+constexpr uint32_t kMpTile = 2048;
+
+// number of row ends consumed at merge-path diagonal `diag`; row_end[i] = end offset of row i
+__device__ __forceinline__ uint32_t mp_rows_before(const uint64_t* __restrict__ row_end, uint32_t nrows,
+                                                   uint64_t nedges, uint64_t diag) {
+    uint64_t lo = diag > nedges ? diag - nedges : 0;
+    uint64_t hi = diag < nrows ? diag : nrows;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (row_end[mid] <= diag - mid - 1)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (uint32_t)lo;
+}
+
+__device__ __forceinline__ uint32_t mp_pad(uint32_t j) { return j + (j >> 5); }  // breaks 32-word strides
+
+struct SumF32 {
+    typedef float T;
+    static __device__ __forceinline__ float identity() { return 0.f; }
+    static __device__ __forceinline__ float combine(float a, float b) { return a + b; }
+};
+
+struct MinU32 {
+    typedef uint32_t T;
+    static __device__ __forceinline__ uint32_t identity() { return kInf; }
+    static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) { return a < b ? a : b; }
+};
+
+template <int kThreads, int kItems, typename T>
+struct MpShared {
+    static constexpr uint32_t kTile = kThreads * kItems;
+    uint32_t end[kTile + 1];
+    T val[kTile + kTile / 32];
+    T wsum[kThreads / 32];
+    int wflag[kThreads / 32];
+    unsigned long long first_start;
+};
+
+// Processes tile `tile`.  gather.template stage<kThreads, kItems>(j0, E, tid, s_val)
+// writes the message of edge j0 + k to s_val[mp_pad(k)] for k < E;
+// emit(row, total) finishes a row.  Begins with a __syncthreads().
+template <int kThreads, int kItems, class Op, class Gather, class Emit>
+__device__ __forceinline__ void mp_tile(MpShared<kThreads, kItems, typename Op::T>& sh,
+                                        const uint64_t* __restrict__ off, uint32_t n, uint64_t m,
+                                        const uint32_t* __restrict__ tile_row, uint64_t tile,
+                                        typename Op::T* __restrict__ tile_head,
+                                        typename Op::T* __restrict__ tile_tail, Gather& gather, Emit& emit) {
+    typedef typename Op::T T;
+    constexpr uint32_t kTile = kThreads * kItems;
+    static_assert(kTile == kMpTile, "tiles share one partition");
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    const uint64_t total = (uint64_t)n + m;
+    const uint64_t d0 = tile * kTile;
+    const uint64_t d1 = d0 + kTile < total ? d0 + kTile : total;
+    const uint32_t i0 = tile_row[tile];
+    const uint32_t i1 = tile_row[tile + 1];
+    const uint64_t j0 = d0 - i0;
+    const uint32_t R = i1 - i0;
+    const uint32_t E = (uint32_t)((d1 - i1) - j0);
+    __syncthreads();  // shared memory of the previous tile is free
+
+    // 1. stage
+    for (uint32_t k = tid; k <= R; k += kThreads) {
+        const uint32_t row = i0 + k;
+        const uint64_t rel = row < n ? off[row + 1] - j0 : (uint64_t)E + 1;
+        sh.end[k] = rel < (uint64_t)E + 1 ? (uint32_t)rel : E + 1;
+    }
+    if (tid == 0) sh.first_start = i0 < n ? off[i0] : m;
+    gather.template stage<kThreads, kItems>(j0, E, tid, sh.val);
+    __syncthreads();
+
+    // 2. walk this thread's slice once
+    const uint32_t items = R + E;
+    const uint32_t ds = min((uint32_t)tid * kItems, items);
+    const uint32_t de = min(ds + kItems, items);
+    uint32_t lo = ds > E ? ds - E : 0, hi = min(ds, R);
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sh.end[mid] <= ds - mid - 1)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    uint32_t i = lo, j = ds - lo;
+    uint32_t cur_end = sh.end[i];
+    T run = Op::identity(), first_val = Op::identity();
+    int first_row = -1;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+        if (ds + q < de) {
+            if (j < cur_end) {
+                run = Op::combine(run, sh.val[mp_pad(j)]);
+                ++j;
+            } else {
+                if (first_row < 0) {
+                    first_row = (int)i;
+                    first_val = run;
+                } else {
+                    emit(i0 + i, run);
+                }
+                run = Op::identity();
+                ++i;
+                cur_end = sh.end[i];
+            }
+        }
+    }
+
+    // 3. segmented inclusive scan of (row ended, partial): (f, v) then (g, w) -> (f|g, g ? w : v + w)
+    T v = run;
+    int f = first_row >= 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T vu = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        const int fu = __shfl_up_sync(0xFFFFFFFFu, f, o);
+        if (lane >= o) {
+            if (!f) v = Op::combine(vu, v);
+            f |= fu;
+        }
+    }
+    if (lane == 31) {
+        sh.wsum[warp] = v;
+        sh.wflag[warp] = f;
+    }
+    __syncthreads();
+    T wc = Op::identity();
+    for (int q = 0; q < warp; ++q) wc = sh.wflag[q] ? sh.wsum[q] : Op::combine(wc, sh.wsum[q]);
+    const T incl = f ? v : Op::combine(wc, v);
+    T excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+    if (lane == 0) excl = wc;
+    if (tid == kThreads - 1) tile_tail[tile] = incl;  // partial of row i1 inside this tile
+
+    // 4. the slice's first finished row, with the carry-in
+    if (first_row >= 0) {
+        const T tot = Op::combine(excl, first_val);
+        if (first_row == 0 && sh.first_start < j0)
+            tile_head[tile] = tot;  // row i0 began in an earlier tile
+        else
+            emit(i0 + (uint32_t)first_row, tot);
+    }
+}
+
+// Tile t's first row, if it began in an earlier tile and ends in t: returns the
+// row and the first tile q0 holding its edges; the caller folds tile_tail[q0..t)
+// and then tile_head[t], in that order.
+__device__ __forceinline__ bool mp_fixup_span(const uint64_t* __restrict__ off, const uint32_t* __restrict__ tile_row,
+                                              uint64_t t, uint32_t n, uint32_t* row, uint64_t* q0) {
+    const uint32_t i0 = tile_row[t];
+    if (i0 >= n || tile_row[t + 1] == i0) return false;  // no row ends in this tile
+    const uint64_t j0 = t * kMpTile - i0;
+    if (off[i0] >= j0) return false;  // began here: finished by the tile itself
+    uint64_t q = t;
+    while (q > 0 && tile_row[q] == i0) --q;  // first tile holding edges of row i0
+    *row = i0;
+    *q0 = q;
+    return true;
+}
+
+// tile boundaries (tiles + 1 entries) of the merge path over a CSR/CSC
+ipg_status mp_partition(const uint64_t* off, uint32_t n, uint64_t m, uint64_t tiles, uint32_t* tile_row,
+                        cudaStream_t st);
+
+inline uint64_t mp_tile_count(uint32_t n, uint64_t m) { return ((uint64_t)n + m + kMpTile - 1) / kMpTile; }
+
+}  // namespace ipg

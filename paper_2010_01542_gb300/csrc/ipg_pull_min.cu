@@ -1,0 +1,211 @@
+// Pull form of a min-combiner superstep (Hashmin, SSSP), used when the frontier
+// is dense.  Push costs a random read and often an atomic per message; when most
+// vertices send, it is cheaper to let every vertex scan its in-edges, as the
+// paper's pull-based "single broadcast" version does for CC (Sec. VI-C), and to
+// reuse PageRank's merge-path tile engine with a min instead of a sum.
+//
+// Superstep s in pull form:
+//   sval[u] = value u sends in s (its snapshot, kInf if u is not a sender);
+//   for every vertex v:  m = min over in-edges (u -> v) of sval[u] (+ w(u,v));
+//   if m < val[v]: val[v] = m and v joins the next frontier.
+// This is the same synchronous superstep as the push form — same values, same
+// next frontier, same counts — because both take the minimum of the same
+// messages and activate on the same strict drop.  Each vertex is finished by
+// exactly one thread (min is exact and order-free), so no atomics on values are
+// needed; next-frontier appends go through a per-CTA shared-memory queue.
+#include "ipg_mergepath.cuh"
+
+namespace ipg {
+namespace {
+
+constexpr int kPmThreads = 256;
+constexpr int kPmItems = 8;
+
+__global__ void sval_scatter_kernel(const uint32_t* __restrict__ F, const uint32_t* __restrict__ fval, uint32_t f,
+                                    uint32_t* __restrict__ sval) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < f; i += stride) sval[F[i]] = fval[i];
+}
+
+// message carried by in-edge j0 + k (kInf when its source does not send)
+template <bool kAddWeight, int kWeightKind>
+struct PmGather {
+    const uint32_t* __restrict__ src;
+    const uint8_t* __restrict__ w8;
+    const uint32_t* __restrict__ w32;
+    const uint32_t* __restrict__ sval;
+    unsigned int* status;
+    template <int kThreads, int kItems>
+    __device__ __forceinline__ void stage(uint64_t j0, uint32_t E, int tid, uint32_t* s_val) const {
+        uint32_t u[kItems], w[kItems];
+#pragma unroll
+        for (int q = 0; q < kItems; ++q) {
+            const uint32_t k = tid + q * kThreads;
+            u[q] = k < E ? __ldcs(src + j0 + k) : 0u;
+            w[q] = 1u;
+            if (kAddWeight && kWeightKind == 1 && k < E) w[q] = __ldcs(w8 + j0 + k);
+            if (kAddWeight && kWeightKind == 2 && k < E) w[q] = __ldcs(w32 + j0 + k);
+        }
+#pragma unroll
+        for (int q = 0; q < kItems; ++q) {
+            const uint32_t k = tid + q * kThreads;
+            if (k < E) {
+                const uint32_t s = __ldg(sval + u[q]);
+                uint32_t msg = s;
+                if (kAddWeight && s != kInf) {
+                    unsigned long long d = (unsigned long long)s + w[q];
+                    if (d >= kInf) {
+                        atomicOr(status, kStatusOverflow);
+                        d = kInf - 1;
+                    }
+                    msg = (uint32_t)d;
+                }
+                s_val[mp_pad(k)] = msg;
+            }
+        }
+    }
+};
+
+template <bool kRecv>
+struct PmEmit {
+    uint32_t* __restrict__ val;
+    uint32_t* q;          // shared-memory queue of this tile's new frontier vertices
+    unsigned int* qn;     // shared-memory queue length
+    unsigned int* nrecv;  // shared-memory receiver count
+    __device__ __forceinline__ void operator()(uint32_t row, uint32_t m) const {
+        if (kRecv && m != kInf) atomicAdd(nrecv, 1u);
+        if (m < val[row]) {
+            val[row] = m;
+            q[atomicAdd(qn, 1u)] = row;
+        }
+    }
+};
+
+template <bool kAddWeight, int kWeightKind, bool kRecv>
+__global__ void __launch_bounds__(kPmThreads) pull_min_kernel(
+    const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ csc_src, const uint8_t* __restrict__ csc_w8,
+    const uint32_t* __restrict__ csc_w32, const uint32_t* __restrict__ sval, uint32_t* __restrict__ val,
+    const uint32_t* __restrict__ tile_row, uint32_t* __restrict__ tile_head, uint32_t* __restrict__ tile_tail,
+    uint64_t tiles, uint32_t n, uint64_t m, uint32_t* __restrict__ next, PushCounters* __restrict__ ctr) {
+    __shared__ MpShared<kPmThreads, kPmItems, uint32_t> sh;
+    __shared__ uint32_t s_q[kMpTile];
+    __shared__ unsigned int s_qn, s_recv, s_base;
+    if (threadIdx.x == 0) {
+        s_qn = 0;
+        s_recv = 0;
+    }
+    PmGather<kAddWeight, kWeightKind> gather{csc_src, csc_w8, csc_w32, sval, &ctr->status};
+    PmEmit<kRecv> emit{val, s_q, &s_qn, &s_recv};
+    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        mp_tile<kPmThreads, kPmItems, MinU32>(sh, csc_off, n, m, tile_row, tile, tile_head, tile_tail, gather, emit);
+        __syncthreads();
+        const unsigned qn = s_qn;
+        if (qn) {
+            if (threadIdx.x == 0) s_base = atomicAdd(&ctr->next_size, qn);
+            __syncthreads();
+            const unsigned base = s_base;
+            for (unsigned k = threadIdx.x; k < qn; k += kPmThreads) next[base + k] = s_q[k];
+            __syncthreads();
+            if (threadIdx.x == 0) s_qn = 0;
+        }
+    }
+    if (kRecv) {
+        __syncthreads();
+        if (threadIdx.x == 0 && s_recv) atomicAdd(&ctr->receivers, (unsigned long long)s_recv);
+    }
+}
+
+template <bool kRecv>
+__global__ void pull_min_fixup_kernel(const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ tile_row,
+                                      const uint32_t* __restrict__ tile_head, const uint32_t* __restrict__ tile_tail,
+                                      uint32_t* __restrict__ val, uint64_t tiles, uint32_t n,
+                                      uint32_t* __restrict__ next, PushCounters* __restrict__ ctr) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += stride) {
+        uint32_t row;
+        uint64_t q;
+        if (!mp_fixup_span(csc_off, tile_row, t, n, &row, &q)) continue;
+        uint32_t mn = kInf;
+        for (; q < t; ++q) mn = min(mn, tile_tail[q]);
+        mn = min(mn, tile_head[t]);
+        if (kRecv && mn != kInf) atomicAdd(&ctr->receivers, 1ull);
+        if (mn < val[row]) {
+            val[row] = mn;
+            next[atomicAdd(&ctr->next_size, 1u)] = row;
+        }
+    }
+}
+
+unsigned pm_grid(ipg_graph* g) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pull_min_kernel<true, 1, false>, kPmThreads, 0) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    uint64_t grid = (uint64_t)sm_count_of(g->device) * per_sm;
+    if (grid > g->pr_tiles) grid = g->pr_tiles;
+    return (unsigned)(grid ? grid : 1);
+}
+
+template <bool kAddWeight, int kWeightKind, bool kRecv>
+void launch(ipg_graph* g, uint32_t* val, uint32_t* next, cudaStream_t st) {
+    pull_min_kernel<kAddWeight, kWeightKind, kRecv><<<pm_grid(g), kPmThreads, 0, st>>>(
+        g->csc_off, g->csc_src, g->csc_w8, g->csc_w, g->sval, val, g->pr_tile_row, (uint32_t*)g->pr_head,
+        (uint32_t*)g->pr_tail, g->pr_tiles, g->n, g->m, next, g->counters);
+}
+
+template <bool kAddWeight, int kWeightKind>
+void launch2(bool recv, ipg_graph* g, uint32_t* val, uint32_t* next, cudaStream_t st) {
+    if (recv)
+        launch<kAddWeight, kWeightKind, true>(g, val, next, st);
+    else
+        launch<kAddWeight, kWeightKind, false>(g, val, next, st);
+}
+
+unsigned small_grid(uint64_t work) {
+    uint64_t b = (work + 255) / 256;
+    if (b < 1) b = 1;
+    return (unsigned)(b < 152 * 16 ? b : 152 * 16);
+}
+
+}  // namespace
+
+ipg_status pull_min_prepare(ipg_graph* g, cudaStream_t st) {
+    IPG_TRY(ensure_pull_partition(g, st));
+    if (!g->sval) IPG_CUDA(cudaMalloc(&g->sval, sizeof(uint32_t) * (g->n ? g->n : 1)));
+    return IPG_OK;
+}
+
+// one pull superstep; the frontier F (f vertices) and its value snapshot fval are
+// the senders; new frontier vertices are appended to next via g->counters
+ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, const uint32_t* F, const uint32_t* fval, uint32_t f,
+                              uint32_t* val, uint32_t* next, cudaStream_t st, cudaEvent_t ev_kernel) {
+    IPG_TRY(pull_min_prepare(g, st));
+    IPG_CUDA(cudaMemsetAsync(g->sval, 0xFF, sizeof(uint32_t) * g->n, st));
+    sval_scatter_kernel<<<small_grid(f), 256, 0, st>>>(F, fval, f, g->sval);
+    IPG_CUDA(cudaGetLastError());
+    if (ev_kernel) IPG_CUDA(cudaEventRecord(ev_kernel, st));
+    if (!sssp)
+        launch2<false, 0>(recv, g, val, next, st);
+    else if (g->csc_w8)
+        launch2<true, 1>(recv, g, val, next, st);
+    else if (g->csc_w)
+        launch2<true, 2>(recv, g, val, next, st);
+    else
+        launch2<true, 0>(recv, g, val, next, st);
+    IPG_CUDA(cudaGetLastError());
+    if (recv)
+        pull_min_fixup_kernel<true><<<small_grid(g->pr_tiles), 256, 0, st>>>(
+            g->csc_off, g->pr_tile_row, (const uint32_t*)g->pr_head, (const uint32_t*)g->pr_tail, val, g->pr_tiles,
+            g->n, next, g->counters);
+    else
+        pull_min_fixup_kernel<false><<<small_grid(g->pr_tiles), 256, 0, st>>>(
+            g->csc_off, g->pr_tile_row, (const uint32_t*)g->pr_head, (const uint32_t*)g->pr_tail, val, g->pr_tiles,
+            g->n, next, g->counters);
+    IPG_CUDA(cudaGetLastError());
+    return IPG_OK;
+}
+
+}  // namespace ipg

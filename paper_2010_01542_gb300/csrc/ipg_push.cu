@@ -78,20 +78,23 @@ __device__ __forceinline__ unsigned long long block_exscan_u64(unsigned long lon
     return s_tmp[warp] + incl - x;
 }
 
-__global__ void hashmin_init_kernel(uint32_t* __restrict__ val, uint32_t* __restrict__ frontier, uint32_t n) {
+// labels are the caller's vertex ids, so the result does not depend on the internal numbering
+__global__ void hashmin_init_kernel(uint32_t* __restrict__ val, uint32_t* __restrict__ frontier,
+                                    const uint32_t* __restrict__ perm, uint32_t n) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        val[v] = (uint32_t)v;
+        val[v] = perm[v];
         frontier[v] = (uint32_t)v;
     }
 }
 
+// `source` is the caller's id; inv maps it to the internal one
 __global__ void sssp_init_kernel(uint32_t* __restrict__ val, uint32_t* __restrict__ frontier, uint32_t n,
-                                 uint32_t source) {
+                                 const uint32_t* __restrict__ inv, uint32_t source) {
+    const uint32_t s = inv[source];
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        val[v] = v == source ? 0u : kInf;
-    if (blockIdx.x == 0 && threadIdx.x == 0) frontier[0] = source;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) val[v] = v == s ? 0u : kInf;
+    if (blockIdx.x == 0 && threadIdx.x == 0) frontier[0] = s;
 }
 
 // pass 1 of the frontier prefix: one degree total per block of 2048 entries
@@ -203,13 +206,24 @@ __global__ void push_partition_kernel(const unsigned long long* __restrict__ pre
     }
 }
 
-template <int kKind, bool kWeighted, bool kRecv>
+constexpr int kEdgesPerThread = 4;  // independent messages in flight per thread
+
+template <int kWeightKind>
+__device__ __forceinline__ uint32_t edge_weight(const uint8_t* __restrict__ w8, const uint32_t* __restrict__ w32,
+                                                unsigned long long p) {
+    if (kWeightKind == 1) return (uint32_t)__ldcs(w8 + p);
+    if (kWeightKind == 2) return __ldcs(w32 + p);
+    return 1u;
+}
+
+// kWeightKind: 0 = no weights (length 1), 1 = u8 weights, 2 = u32 weights
+template <int kKind, int kWeightKind, bool kRecv>
 __global__ void __launch_bounds__(kPushThreads) push_relax_kernel(
     const unsigned long long* __restrict__ prefix, const unsigned long long* __restrict__ rowstart,
     const uint32_t* __restrict__ fval, const uint32_t* __restrict__ tile_row, const uint32_t* __restrict__ col,
-    const uint32_t* __restrict__ wt, uint32_t* __restrict__ val, uint32_t* __restrict__ stamp,
-    uint32_t* __restrict__ rstamp, uint32_t* __restrict__ next, PushCounters* __restrict__ ctr, uint32_t f,
-    uint32_t tag) {
+    const uint8_t* __restrict__ w8, const uint32_t* __restrict__ w32, uint32_t* __restrict__ val,
+    uint32_t* __restrict__ stamp, uint32_t* __restrict__ rstamp, uint32_t* __restrict__ next,
+    PushCounters* __restrict__ ctr, uint32_t f, uint32_t tag) {
     __shared__ uint32_t s_start[kPushTile + 1];
     __shared__ unsigned long long s_base[kPushTile + 1];
     __shared__ uint32_t s_val[kPushTile + 1];
@@ -241,51 +255,63 @@ __global__ void __launch_bounds__(kPushThreads) push_relax_kernel(
             }
         }
         __syncthreads();
-        for (uint32_t k0 = 0; k0 < Et; k0 += kPushThreads) {
-            const uint32_t k = k0 + tid;
-            bool app = false, rcv = false;
-            uint32_t v = 0;
-            if (k < Et) {
-                // row of edge k: last row whose start is <= k
-                uint32_t lo = 0, hi = R;
-                while (lo < hi) {
-                    uint32_t mid = (lo + hi + 1) >> 1;
-                    if (s_start[mid] <= k)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
-                }
-                const unsigned long long p = s_base[lo] + k;
-                v = __ldcs(col + p);
-                uint32_t cand;
-                if (kKind == kHashmin) {
-                    cand = s_val[lo];
-                } else {
-                    unsigned long long d = (unsigned long long)s_val[lo] + (kWeighted ? __ldcs(wt + p) : 1u);
-                    if (d >= kInf) {
-                        atomicOr(&ctr->status, kStatusOverflow);
-                        d = kInf - 1;
+        for (uint32_t k0 = 0; k0 < Et; k0 += kPushThreads * kEdgesPerThread) {
+            uint32_t v[kEdgesPerThread], cand[kEdgesPerThread], cur[kEdgesPerThread];
+            bool ok[kEdgesPerThread];
+#pragma unroll
+            for (int q = 0; q < kEdgesPerThread; ++q) {
+                const uint32_t k = k0 + tid + q * kPushThreads;
+                ok[q] = k < Et;
+                v[q] = 0;
+                cand[q] = 0;
+                if (ok[q]) {
+                    // row of edge k: the last row whose start is <= k
+                    uint32_t lo = 0, hi = R;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if (s_start[mid] <= k)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
                     }
-                    cand = (uint32_t)d;
-                }
-                if (kRecv) rcv = atomicExch(&rstamp[v], tag) != tag;
-                const uint32_t cur = val[v];  // may be stale-high, never below the true value
-                if (cand < cur) {
-                    const uint32_t old = atomicMin(&val[v], cand);
-                    if (cand < old) app = atomicExch(&stamp[v], tag) != tag;
+                    const unsigned long long p = s_base[lo] + k;
+                    v[q] = __ldcs(col + p);
+                    if (kKind == kHashmin) {
+                        cand[q] = s_val[lo];
+                    } else {
+                        unsigned long long d = (unsigned long long)s_val[lo] + edge_weight<kWeightKind>(w8, w32, p);
+                        if (d >= kInf) {
+                            atomicOr(&ctr->status, kStatusOverflow);
+                            d = kInf - 1;
+                        }
+                        cand[q] = (uint32_t)d;
+                    }
                 }
             }
-            const unsigned mask = __ballot_sync(0xFFFFFFFFu, app);
-            if (mask) {
-                const int leader = __ffs(mask) - 1;
-                uint32_t pos = 0;
-                if (lane == leader) pos = atomicAdd(&ctr->next_size, (unsigned)__popc(mask));
-                pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-                if (app) next[pos + __popc(mask & ((1u << lane) - 1u))] = v;
-            }
-            if (kRecv) {
-                const unsigned rm = __ballot_sync(0xFFFFFFFFu, rcv);
-                if (lane == 0 && rm) atomicAdd(&ctr->receivers, (unsigned long long)__popc(rm));
+#pragma unroll
+            for (int q = 0; q < kEdgesPerThread; ++q) cur[q] = ok[q] ? val[v[q]] : 0u;  // stale-high, never low
+#pragma unroll
+            for (int q = 0; q < kEdgesPerThread; ++q) {
+                bool app = false, rcv = false;
+                if (ok[q]) {
+                    if (kRecv) rcv = atomicExch(&rstamp[v[q]], tag) != tag;
+                    if (cand[q] < cur[q]) {
+                        const uint32_t old = atomicMin(&val[v[q]], cand[q]);
+                        if (cand[q] < old) app = atomicExch(&stamp[v[q]], tag) != tag;
+                    }
+                }
+                const unsigned mask = __ballot_sync(0xFFFFFFFFu, app);
+                if (mask) {
+                    const int leader = __ffs(mask) - 1;
+                    uint32_t pos = 0;
+                    if (lane == leader) pos = atomicAdd(&ctr->next_size, (unsigned)__popc(mask));
+                    pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+                    if (app) next[pos + __popc(mask & ((1u << lane) - 1u))] = v[q];
+                }
+                if (kRecv) {
+                    const unsigned rm = __ballot_sync(0xFFFFFFFFu, rcv);
+                    if (lane == 0 && rm) atomicAdd(&ctr->receivers, (unsigned long long)__popc(rm));
+                }
             }
         }
     }
@@ -303,32 +329,39 @@ int sm_count(int dev) {
     return v;
 }
 
-template <int kKind, bool kWeighted, bool kRecv>
+template <int kKind, int kWeightKind, bool kRecv>
 void launch_relax(unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next, uint32_t f,
                   uint32_t tag) {
-    push_relax_kernel<kKind, kWeighted, kRecv><<<grid, kPushThreads, 0, st>>>(
-        g->fr_prefix, g->fr_rowstart, g->fr_val, g->push_tile_row, g->col, g->w, val, g->stamp, g->rstamp, next,
+    push_relax_kernel<kKind, kWeightKind, kRecv><<<grid, kPushThreads, 0, st>>>(
+        g->fr_prefix, g->fr_rowstart, g->fr_val, g->push_tile_row, g->col, g->w8, g->w, val, g->stamp, g->rstamp, next,
         g->counters, f, tag);
 }
 
-void relax_dispatch(int kind, bool weighted, bool recv, unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val,
-                    uint32_t* next, uint32_t f, uint32_t tag) {
-    if (kind == kHashmin) {
-        if (recv)
-            launch_relax<kHashmin, false, true>(grid, st, g, val, next, f, tag);
-        else
-            launch_relax<kHashmin, false, false>(grid, st, g, val, next, f, tag);
-    } else if (weighted) {
-        if (recv)
-            launch_relax<kSssp, true, true>(grid, st, g, val, next, f, tag);
-        else
-            launch_relax<kSssp, true, false>(grid, st, g, val, next, f, tag);
-    } else {
-        if (recv)
-            launch_relax<kSssp, false, true>(grid, st, g, val, next, f, tag);
-        else
-            launch_relax<kSssp, false, false>(grid, st, g, val, next, f, tag);
-    }
+template <int kKind, int kWeightKind>
+void launch_relax2(bool recv, unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next,
+                   uint32_t f, uint32_t tag) {
+    if (recv)
+        launch_relax<kKind, kWeightKind, true>(grid, st, g, val, next, f, tag);
+    else
+        launch_relax<kKind, kWeightKind, false>(grid, st, g, val, next, f, tag);
+}
+
+void relax_dispatch(int kind, bool recv, unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next,
+                    uint32_t f, uint32_t tag) {
+    if (kind == kHashmin)
+        launch_relax2<kHashmin, 0>(recv, grid, st, g, val, next, f, tag);
+    else if (g->w8)
+        launch_relax2<kSssp, 1>(recv, grid, st, g, val, next, f, tag);
+    else if (g->w)
+        launch_relax2<kSssp, 2>(recv, grid, st, g, val, next, f, tag);
+    else
+        launch_relax2<kSssp, 0>(recv, grid, st, g, val, next, f, tag);
+}
+
+__global__ void unpermute_u32_kernel(const uint32_t* __restrict__ in, const uint32_t* __restrict__ inv, uint32_t n,
+                                     uint32_t* __restrict__ out) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) out[v] = in[inv[v]];
 }
 
 ipg_status ensure_events_push(size_t count, cudaEvent_t** evs) {
@@ -346,14 +379,14 @@ ipg_status ensure_events_push(size_t count, cudaEvent_t** evs) {
     return IPG_OK;
 }
 
-ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* val, ipg_stats* stats, cudaStream_t st) {
+ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_stats* stats, cudaStream_t st) {
     stats_begin(stats);
     const char* name = kind == kHashmin ? "ipg_hashmin_cc" : "ipg_sssp";
     if (!g) return set_error(IPG_EINVAL, "%s: graph is NULL", name);
     if (kind == kHashmin && g->directed)
         return set_error(IPG_EINVAL, "%s: Hashmin components need an undirected graph (directed = 0)", name);
     if (kind == kSssp && source >= g->n) return set_error(IPG_EINVAL, "%s: source %u >= n = %u", name, source, g->n);
-    if (g->n && !val) return set_error(IPG_EINVAL, "%s: output is NULL", name);
+    if (g->n && !out) return set_error(IPG_EINVAL, "%s: output is NULL", name);
     DeviceGuard guard(g->device);
     if (!guard.ok) return set_error(IPG_ECUDA, "%s: cannot select the graph's device", name);
     const uint32_t n = g->n;
@@ -369,6 +402,7 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* val, ipg_
         return IPG_OK;
     }
     IPG_TRY(ensure_push_workspace(g, recv));
+    uint32_t* val = g->val;
     cudaEvent_t* ev = nullptr;
     if (timing) IPG_TRY(ensure_events_push(3, &ev));
     const int sms = sm_count(g->device);
@@ -380,10 +414,10 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* val, ipg_
     IPG_CUDA(cudaMemsetAsync(&g->counters->status, 0, sizeof(unsigned), st));
     uint32_t f;
     if (kind == kHashmin) {
-        hashmin_init_kernel<<<grid_cap(n), 256, 0, st>>>(val, g->frontier[0], n);
+        hashmin_init_kernel<<<grid_cap(n), 256, 0, st>>>(val, g->frontier[0], g->perm, n);
         f = n;
     } else {
-        sssp_init_kernel<<<grid_cap(n), 256, 0, st>>>(val, g->frontier[0], n, source);
+        sssp_init_kernel<<<grid_cap(n), 256, 0, st>>>(val, g->frontier[0], n, g->inv, source);
         f = 1;
     }
     IPG_CUDA(cudaGetLastError());
@@ -399,11 +433,27 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* val, ipg_
         fr_scan_kernel<<<1, kScanThreads, 0, st>>>(g->block_sums, nb, f, g->fr_prefix, g->counters);
         fr_write_kernel<<<nb, kFrThreads, 0, st>>>(g->frontier[cur], f, g->off, val, g->block_sums, g->fr_prefix,
                                                    g->fr_rowstart, g->fr_val);
-        push_partition_kernel<<<part_grid, 256, 0, st>>>(g->fr_prefix, f, g->counters, g->push_tile_row);
         IPG_CUDA(cudaGetLastError());
-        if (timing) IPG_CUDA(cudaEventRecord(ev[1], st));
-        relax_dispatch(kind, g->weighted != 0, recv, relax_grid, st, g, val, g->frontier[cur ^ 1], f, s + 1);
-        IPG_CUDA(cudaGetLastError());
+        // direction: a superstep whose messages reach m / pull_divisor runs in pull form
+        bool pull = false;
+        const long long div = tuning().pull_divisor;
+        if (div > 0 && g->m) {
+            IPG_CUDA(cudaMemcpyAsync(&g->h_counters->edges, &g->counters->edges, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, st));
+            IPG_CUDA(cudaStreamSynchronize(st));
+            const unsigned long long es = g->h_counters->edges;
+            pull = es > 0 && (double)es * (double)div >= (double)g->m;
+        }
+        if (pull) {
+            IPG_TRY(pull_min_superstep(g, kind == kSssp, recv, g->frontier[cur], g->fr_val, f, val,
+                                       g->frontier[cur ^ 1], st, timing ? ev[1] : nullptr));
+        } else {
+            push_partition_kernel<<<part_grid, 256, 0, st>>>(g->fr_prefix, f, g->counters, g->push_tile_row);
+            IPG_CUDA(cudaGetLastError());
+            if (timing) IPG_CUDA(cudaEventRecord(ev[1], st));
+            relax_dispatch(kind, recv, relax_grid, st, g, val, g->frontier[cur ^ 1], f, s + 1);
+            IPG_CUDA(cudaGetLastError());
+        }
         if (timing) IPG_CUDA(cudaEventRecord(ev[2], st));
         IPG_CUDA(cudaMemcpyAsync(g->h_counters, g->counters, sizeof(PushCounters), cudaMemcpyDeviceToHost, st));
         IPG_CUDA(cudaStreamSynchronize(st));
@@ -446,6 +496,9 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* val, ipg_
         cur ^= 1;
         ++s;
     }
+    unpermute_u32_kernel<<<grid_cap(n), 256, 0, st>>>(val, g->inv, n, out);
+    IPG_CUDA(cudaGetLastError());
+    IPG_CUDA(cudaStreamSynchronize(st));
     if (stats) stats->count = count;
     return IPG_OK;
 }
@@ -455,6 +508,7 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* val, ipg_
 ipg_status ensure_push_workspace(ipg_graph* g, bool receivers) {
     const uint32_t n = g->n;
     if (!g->stamp) {
+        IPG_CUDA(cudaMalloc(&g->val, sizeof(uint32_t) * n));
         IPG_CUDA(cudaMalloc(&g->stamp, sizeof(uint32_t) * n));
         IPG_CUDA(cudaMalloc(&g->frontier[0], sizeof(uint32_t) * n));
         IPG_CUDA(cudaMalloc(&g->frontier[1], sizeof(uint32_t) * n));

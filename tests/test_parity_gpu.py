@@ -30,6 +30,18 @@ def ipg():
     return ipg
 
 
+ALWAYS_PULL = 1 << 40  # any superstep with a message runs in pull form
+
+
+@pytest.fixture(params=["auto", "push", "pull"])
+def direction(request, ipg):
+    """Runs a Hashmin/SSSP test with the automatic push/pull switch, always push, or always pull."""
+    old = ipg.ipg_get_tuning("pull_divisor")
+    ipg.ipg_set_tuning("pull_divisor", {"auto": old, "push": 0, "pull": ALWAYS_PULL}[request.param])
+    yield request.param
+    ipg.ipg_set_tuning("pull_divisor", old)
+
+
 def _create(ipg, g, directed=None):
     d = g.directed if directed is None else directed
     return ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, d)
@@ -115,12 +127,12 @@ def test_pagerank_update_counts(ipg, updates):
     check_pagerank(ipg, gen.rmat(10, 8, seed=4), updates)
 
 
-def test_hashmin_adversarial(ipg):
+def test_hashmin_adversarial(ipg, direction):
     for name, g in _adversarial(True):
         check_hashmin(ipg, g)
 
 
-def test_sssp_adversarial(ipg):
+def test_sssp_adversarial(ipg, direction):
     for name, g in _adversarial(False):
         for src in sorted({0, g.n - 1, g.n // 2}):
             check_sssp(ipg, g, src, weights=None)
@@ -129,7 +141,7 @@ def test_sssp_adversarial(ipg):
 
 
 @pytest.mark.parametrize("seed", range(12))
-def test_random_multigraphs(ipg, seed):
+def test_random_multigraphs(ipg, seed, direction):
     rng = np.random.default_rng(seed)
     n = int(rng.integers(1, 3000))
     m = int(rng.integers(0, 25000))
@@ -143,7 +155,7 @@ def test_random_multigraphs(ipg, seed):
 
 
 @pytest.mark.parametrize("scale", [4, 6, 8, 10, 12, 14])
-def test_rmat_scales(ipg, scale):
+def test_rmat_scales(ipg, scale, direction):
     g = gen.rmat(scale, 16, seed=scale, weighted=True)
     check_pagerank(ipg, g)
     src = gen.max_out_degree_vertex(g)
@@ -187,7 +199,15 @@ def test_device_entry_points_match_host(ipg):
 # errors
 
 
-def test_errors(ipg):
+def test_tuning_knobs(ipg):
+    assert ipg.ipg_get_tuning("pull_divisor") >= 0
+    with pytest.raises(ipg.IpgError):
+        ipg.ipg_set_tuning("no_such_knob", 1)
+    with pytest.raises(ipg.IpgError):
+        ipg.ipg_set_tuning("pull_divisor", -1)
+
+
+def test_errors(ipg, direction):
     good = gen.csr_from_edges(3, [0, 1], [1, 2])
     with pytest.raises(ipg.IpgError) as e:
         ipg.ipg_graph_create(np.array([0, 2, 1, 2], np.uint64), good.cols, None, 3, 2, True)
@@ -225,7 +245,7 @@ def test_config_pagerank_scale16(ipg):
     check_pagerank(ipg, g, 10)
 
 
-def test_config_hashmin_scale20(ipg):
+def test_config_hashmin_scale20(ipg, direction):
     """Hashmin CC on the undirected R-MAT scale 20, edge factor 16, seed 1."""
     g = gen.rmat(20, 16, seed=1, undirected=True)
     check_hashmin(ipg, g)
