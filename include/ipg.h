@@ -73,6 +73,7 @@ typedef struct {
 
 #define IPG_STAT_RECEIVERS 1u /* count receivers (costs one extra atomic per message) */
 #define IPG_STAT_TIMING 2u    /* time every superstep with CUDA events */
+#define IPG_STAT_PULL 4u      /* set by the library: the superstep ran in pull form */
 
 /* Caller-owned statistics buffer.  The library writes min(count, cap) records
  * and sets `count` to the number of supersteps executed, which is also the

@@ -23,7 +23,7 @@ __all__ = [
     "IpgError", "IpgLibraryMissing", "SuperstepStats", "Graph", "ipg_graph_create", "ipg_graph_create_dev",
     "ipg_graph_destroy", "ipg_graph_info", "ipg_pagerank", "ipg_pagerank_dev", "ipg_hashmin_cc",
     "ipg_hashmin_cc_dev", "ipg_sssp", "ipg_sssp_dev", "ipg_last_error", "ipg_version",
-    "IPG_STAT_RECEIVERS", "IPG_STAT_TIMING", "INF", "load_library",
+    "IPG_STAT_RECEIVERS", "IPG_STAT_TIMING", "IPG_STAT_PULL", "INF", "load_library",
 ]
 
 IPG_OK, IPG_EINVAL, IPG_ENOMEM, IPG_ECUDA, IPG_ETIMEOUT, IPG_EDEVICE, IPG_ENOTSUP, IPG_EOVERFLOW = range(8)
@@ -31,6 +31,7 @@ STATUS_NAMES = ["IPG_OK", "IPG_EINVAL", "IPG_ENOMEM", "IPG_ECUDA", "IPG_ETIMEOUT
                 "IPG_EOVERFLOW"]
 IPG_STAT_RECEIVERS = 1
 IPG_STAT_TIMING = 2
+IPG_STAT_PULL = 4
 INF = 0xFFFFFFFF
 
 

@@ -66,78 +66,84 @@ struct MpShared {
     unsigned long long first_start;
 };
 
-// Processes tile `tile`.  gather.template stage<kThreads, kItems>(j0, E, tid, s_val)
-// writes the message of edge j0 + k to s_val[mp_pad(k)] for k < E;
-// emit(row, total) finishes a row.  Begins with a __syncthreads().
-template <int kThreads, int kItems, class Op, class Gather, class Emit>
-__device__ __forceinline__ void mp_tile(MpShared<kThreads, kItems, typename Op::T>& sh,
-                                        const uint64_t* __restrict__ off, uint32_t n, uint64_t m,
-                                        const uint32_t* __restrict__ tile_row, uint64_t tile,
-                                        typename Op::T* __restrict__ tile_head,
-                                        typename Op::T* __restrict__ tile_tail, Gather& gather, Emit& emit) {
+// Geometry of merge-path tile `tile`: rows [i0, i1) end in it, edges [j0, j0 + E) lie in it.
+struct MpGeom {
+    uint32_t i0, i1, R, E;
+    uint64_t j0;
+};
+
+__device__ __forceinline__ MpGeom mp_geom(const uint32_t* __restrict__ tile_row, uint64_t tile, uint32_t n,
+                                          uint64_t m) {
+    const uint64_t total = (uint64_t)n + m;
+    const uint64_t d0 = tile * kMpTile;
+    const uint64_t d1 = d0 + kMpTile < total ? d0 + kMpTile : total;
+    MpGeom g;
+    g.i0 = tile_row[tile];
+    g.i1 = tile_row[tile + 1];
+    g.j0 = d0 - g.i0;
+    g.R = g.i1 - g.i0;
+    g.E = (uint32_t)((d1 - g.i1) - g.j0);
+    return g;
+}
+
+// row end of row i0 + k relative to j0, clamped past the tile (E + 1 for the row
+// after the last one)
+__device__ __forceinline__ uint32_t mp_rel_end(const uint64_t* __restrict__ off, const MpGeom& g, uint32_t k,
+                                               uint32_t n) {
+    const uint32_t row = g.i0 + k;
+    const uint64_t rel = row < n ? off[row + 1] - g.j0 : (uint64_t)g.E + 1;
+    return rel < (uint64_t)g.E + 1 ? (uint32_t)rel : g.E + 1;
+}
+
+// Steps 2-4 on a staged tile: end[0..R] (relative row ends), val[mp_pad(k)] for
+// k < E, and first_start = offset of row i0, all visible to every thread.
+// Contains one __syncthreads().
+template <int kThreads, int kItems, class Op, class Emit>
+__device__ __forceinline__ void mp_reduce(const uint32_t* end, const typename Op::T* val, const MpGeom& g,
+                                          unsigned long long first_start, typename Op::T* wsum, int* wflag,
+                                          uint64_t tile, typename Op::T* __restrict__ tile_head,
+                                          typename Op::T* __restrict__ tile_tail, Emit& emit) {
     typedef typename Op::T T;
-    constexpr uint32_t kTile = kThreads * kItems;
-    static_assert(kTile == kMpTile, "tiles share one partition");
+    static_assert(kThreads * kItems == (int)kMpTile, "tiles share one partition");
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
-    const uint64_t total = (uint64_t)n + m;
-    const uint64_t d0 = tile * kTile;
-    const uint64_t d1 = d0 + kTile < total ? d0 + kTile : total;
-    const uint32_t i0 = tile_row[tile];
-    const uint32_t i1 = tile_row[tile + 1];
-    const uint64_t j0 = d0 - i0;
-    const uint32_t R = i1 - i0;
-    const uint32_t E = (uint32_t)((d1 - i1) - j0);
-    __syncthreads();  // shared memory of the previous tile is free
-
-    // 1. stage
-    for (uint32_t k = tid; k <= R; k += kThreads) {
-        const uint32_t row = i0 + k;
-        const uint64_t rel = row < n ? off[row + 1] - j0 : (uint64_t)E + 1;
-        sh.end[k] = rel < (uint64_t)E + 1 ? (uint32_t)rel : E + 1;
-    }
-    if (tid == 0) sh.first_start = i0 < n ? off[i0] : m;
-    gather.template stage<kThreads, kItems>(j0, E, tid, sh.val);
-    __syncthreads();
-
-    // 2. walk this thread's slice once
-    const uint32_t items = R + E;
+    // walk this thread's slice once
+    const uint32_t items = g.R + g.E;
     const uint32_t ds = min((uint32_t)tid * kItems, items);
     const uint32_t de = min(ds + kItems, items);
-    uint32_t lo = ds > E ? ds - E : 0, hi = min(ds, R);
+    uint32_t lo = ds > g.E ? ds - g.E : 0, hi = min(ds, g.R);
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (sh.end[mid] <= ds - mid - 1)
+        if (end[mid] <= ds - mid - 1)
             lo = mid + 1;
         else
             hi = mid;
     }
     uint32_t i = lo, j = ds - lo;
-    uint32_t cur_end = sh.end[i];
+    uint32_t cur_end = end[i];
     T run = Op::identity(), first_val = Op::identity();
     int first_row = -1;
 #pragma unroll
     for (int q = 0; q < kItems; ++q) {
         if (ds + q < de) {
             if (j < cur_end) {
-                run = Op::combine(run, sh.val[mp_pad(j)]);
+                run = Op::combine(run, val[mp_pad(j)]);
                 ++j;
             } else {
                 if (first_row < 0) {
                     first_row = (int)i;
                     first_val = run;
                 } else {
-                    emit(i0 + i, run);
+                    emit(g.i0 + i, run);
                 }
                 run = Op::identity();
                 ++i;
-                cur_end = sh.end[i];
+                cur_end = end[i];
             }
         }
     }
-
-    // 3. segmented inclusive scan of (row ended, partial): (f, v) then (g, w) -> (f|g, g ? w : v + w)
+    // segmented inclusive scan of (row ended, partial): (f, v) then (g, w) -> (f|g, g ? w : v + w)
     T v = run;
     int f = first_row >= 0;
 #pragma unroll
@@ -150,25 +156,44 @@ __device__ __forceinline__ void mp_tile(MpShared<kThreads, kItems, typename Op::
         }
     }
     if (lane == 31) {
-        sh.wsum[warp] = v;
-        sh.wflag[warp] = f;
+        wsum[warp] = v;
+        wflag[warp] = f;
     }
     __syncthreads();
     T wc = Op::identity();
-    for (int q = 0; q < warp; ++q) wc = sh.wflag[q] ? sh.wsum[q] : Op::combine(wc, sh.wsum[q]);
+    for (int q = 0; q < warp; ++q) wc = wflag[q] ? wsum[q] : Op::combine(wc, wsum[q]);
     const T incl = f ? v : Op::combine(wc, v);
     T excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
     if (lane == 0) excl = wc;
     if (tid == kThreads - 1) tile_tail[tile] = incl;  // partial of row i1 inside this tile
-
-    // 4. the slice's first finished row, with the carry-in
+    // the slice's first finished row, with the carry-in
     if (first_row >= 0) {
         const T tot = Op::combine(excl, first_val);
-        if (first_row == 0 && sh.first_start < j0)
+        if (first_row == 0 && first_start < g.j0)
             tile_head[tile] = tot;  // row i0 began in an earlier tile
         else
-            emit(i0 + (uint32_t)first_row, tot);
+            emit(g.i0 + (uint32_t)first_row, tot);
     }
+}
+
+// Processes tile `tile` with plain staging.  gather.template stage<kThreads, kItems>
+// (j0, E, tid, s_val) writes the message of edge j0 + k to s_val[mp_pad(k)] for
+// k < E; emit(row, total) finishes a row.  Begins with a __syncthreads().
+template <int kThreads, int kItems, class Op, class Gather, class Emit>
+__device__ __forceinline__ void mp_tile(MpShared<kThreads, kItems, typename Op::T>& sh,
+                                        const uint64_t* __restrict__ off, uint32_t n, uint64_t m,
+                                        const uint32_t* __restrict__ tile_row, uint64_t tile,
+                                        typename Op::T* __restrict__ tile_head,
+                                        typename Op::T* __restrict__ tile_tail, Gather& gather, Emit& emit) {
+    const MpGeom g = mp_geom(tile_row, tile, n, m);
+    const int tid = threadIdx.x;
+    __syncthreads();  // shared memory of the previous tile is free
+    for (uint32_t k = tid; k <= g.R; k += kThreads) sh.end[k] = mp_rel_end(off, g, k, n);
+    if (tid == 0) sh.first_start = g.i0 < n ? off[g.i0] : m;
+    gather.template stage<kThreads, kItems>(g.j0, g.E, tid, sh.val);
+    __syncthreads();
+    mp_reduce<kThreads, kItems, Op>(sh.end, sh.val, g, sh.first_start, sh.wsum, sh.wflag, tile, tile_head, tile_tail,
+                                    emit);
 }
 
 // Tile t's first row, if it began in an earlier tile and ends in t: returns the

@@ -465,7 +465,7 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
         if (stats) {
             ipg_superstep_stats r{};
             r.superstep = s;
-            r.flags = (recv ? IPG_STAT_RECEIVERS : 0u) | (timing ? IPG_STAT_TIMING : 0u);
+            r.flags = (recv ? IPG_STAT_RECEIVERS : 0u) | (timing ? IPG_STAT_TIMING : 0u) | (pull ? IPG_STAT_PULL : 0u);
             r.active = s == 0 ? n : (recv ? prev_receivers : 0);
             r.senders = f;
             r.messages_sent = h.edges;

@@ -207,6 +207,7 @@ def test_tuning_knobs(ipg):
         ipg.ipg_set_tuning("pull_divisor", -1)
 
 
+
 def test_errors(ipg, direction):
     good = gen.csr_from_edges(3, [0, 1], [1, 2])
     with pytest.raises(ipg.IpgError) as e:
