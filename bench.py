@@ -205,9 +205,11 @@ def kernel_hash(files):
     return h.hexdigest()[:16]
 
 
+_CSRC = "paper_2010_01542_gb300/csrc/"
 KERNEL_FILES = {
-    "pr_pull_kernel": ["paper_2010_01542_gb300/csrc/ipg_pagerank.cu", "paper_2010_01542_gb300/csrc/ipg_internal.cuh"],
-    "push_relax_kernel": ["paper_2010_01542_gb300/csrc/ipg_push.cu", "paper_2010_01542_gb300/csrc/ipg_internal.cuh"],
+    "pr_pull_kernel": [_CSRC + "ipg_pagerank.cu", _CSRC + "ipg_mergepath.cuh", _CSRC + "ipg_internal.cuh"],
+    "pull_min_kernel": [_CSRC + "ipg_pull_min.cu", _CSRC + "ipg_mergepath.cuh", _CSRC + "ipg_internal.cuh"],
+    "push_relax_kernel": [_CSRC + "ipg_push.cu", _CSRC + "ipg_internal.cuh"],
 }
 
 
