@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["billion", "batch"], default="billion",
+                   help="billion: the default bench line; batch: 256-source batched SSSP vs one at a time")
+    p.add_argument("--batch-sources", type=int, default=256)
     p.add_argument("--scale", type=int, default=26)
     p.add_argument("--edge-factor", type=int, default=28)
     p.add_argument("--seed", type=int, default=1)
@@ -430,10 +433,76 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(a):
+    """Batched SSSP: k seeded uniform-random sources on a directed weighted R-MAT graph
+    (default scale 22, EF 16), one ipg_sssp_batch_dev call per step, against the same k
+    sources run one at a time with ipg_sssp_dev; results compared on the device."""
+    import torch
+
+    import gen
+    import paper_2010_01542_gb300 as ipg
+
+    world, rank, local = dist_init(a)
+    ipg.load_library()
+    scale = a.scale if a.scale != 26 else 22
+    ef = a.edge_factor if a.edge_factor != 28 else 16
+    dg = gen.rmat_device(scale, ef, seed=a.seed, weighted=True, device=local)
+    n, m = dg.n, dg.m
+    stream = torch.cuda.Stream()
+    h = ipg.ipg_graph_create_dev(dg.offsets, dg.cols, dg.weights, n, m, True, stream=stream)
+    del dg
+    k = a.batch_sources
+    sources = np.random.default_rng(a.seed).integers(0, n, size=k).astype(np.uint32)
+    out = torch.empty(k * n, dtype=torch.int32, device="cuda")
+    single = torch.empty(n, dtype=torch.int32, device="cuda")
+    for _ in range(max(a.warmup, 1)):
+        ipg.ipg_sssp_batch_dev(h, sources, out, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record(stream)
+    for _ in range(a.steps):
+        steps_b = ipg.ipg_sssp_batch_dev(h, sources, out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = all_max(e0.elapsed_time(e1) / a.steps, world)
+    # one at a time, same sources, checked against the batch rows
+    ipg.ipg_sssp_dev(h, int(sources[0]), single, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    counts = []
+    for i, s in enumerate(sources):
+        c, _ = ipg.ipg_sssp_dev(h, int(s), single, stream=stream)
+        counts.append(c)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_single = all_max(e0.elapsed_time(e1), world)
+    equal = True
+    for i, s in enumerate(sources):
+        ipg.ipg_sssp_dev(h, int(s), single, stream=stream)
+        torch.cuda.synchronize()
+        equal &= bool(torch.equal(out[i * n:(i + 1) * n], single)) and counts[i] == int(steps_b[i])
+    if rank == 0:
+        line = {"metric": "SSSP queries/s, batched (k sources per call) vs one at a time", "unit": "queries/s",
+                "value": round(world * k / (t_batch / 1e3), 1), "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": round(t_batch, 3), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": f"rmat{scale}-ef{ef} directed weighted[1,255] seed {a.seed}, "
+                                       f"{k} uniform random sources (seed {a.seed})", "n": n, "m": m, "k": k},
+                "one_at_a_time": {"value": round(world * k / (t_single / 1e3), 1), "unit": "queries/s",
+                                  "ms_total": round(t_single, 2)},
+                "speedup": round(t_single / t_batch, 2), "results_equal": equal,
+                "supersteps": {"min": int(steps_b.min()), "max": int(steps_b.max())}}
+        print(json.dumps(line), flush=True)
+    h.destroy()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_batch(a)
     else:
         run_ours(a)
 

@@ -147,6 +147,24 @@ ipg_status ipg_sssp(ipg_graph* g, uint32_t source, uint32_t* dist_out, ipg_stats
 ipg_status ipg_sssp_dev(ipg_graph* g, uint32_t source, uint32_t* dist_dev, ipg_stats* stats, void* stream);
 
 /*
+ * ipg_sssp_batch — k independent SSSP runs, each exactly as ipg_sssp from
+ * sources[i], executed together on one graph (batched queries; not in the
+ * paper, whose runs are one source at a time).  Groups of 32 sources share each
+ * superstep: the 32 values of a vertex sit in one 128-byte line, so one
+ * coalesced read per in-edge serves the whole group.
+ *   sources         host, k vertex ids < n (repeats allowed), else IPG_EINVAL;
+ *   dist_out        host, k * n uint32: row i holds the distances from sources[i]
+ *                   (UINT32_MAX = unreachable);
+ *   supersteps_out  host, k entries or NULL: the superstep count of each run.
+ * ipg_sssp_batch_dev writes the k * n result to device memory on `stream`.
+ * Uses 2 x 128 bytes per vertex of device workspace, kept with the graph.
+ */
+ipg_status ipg_sssp_batch(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_out,
+                          uint32_t* supersteps_out);
+ipg_status ipg_sssp_batch_dev(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_dev,
+                              uint32_t* supersteps_out, void* stream);
+
+/*
  * ipg_sssp_noalloc — the same SSSP as ipg_sssp, for callers that may not
  * allocate device memory (the paper has no counterpart to this call).
  * Callers whose device memory belongs to another allocator (a framework's

@@ -326,3 +326,46 @@ def ipg_get_tuning(name: str) -> int:
 
 
 __all__ += ["ipg_set_tuning", "ipg_get_tuning"]
+
+
+def _sources_arr(sources, n):
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.uint32).ravel())
+    return src
+
+
+def ipg_sssp_batch(g: Graph, sources, dist_out: Optional[np.ndarray] = None):
+    """k SSSP runs (one per source) together.  Returns (dist[k, n] uint32, supersteps[k])."""
+    lib = load_library()
+    n = ipg_graph_info(g)["n"]
+    src = _sources_arr(sources, n)
+    k = src.size
+    out = np.empty((k, n), dtype=np.uint32) if dist_out is None else dist_out
+    if out.dtype != np.uint32 or not out.flags.c_contiguous or out.size < k * n:
+        raise ValueError("dist_out must be a contiguous uint32 array of k * n entries")
+    steps = np.zeros(k, dtype=np.uint32)
+    fn = lib.ipg_sssp_batch
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    _check(fn(g.handle, src.ctypes.data if k else None, k, out.ctypes.data if k * n else None,
+              steps.ctypes.data if k else None))
+    return out, steps
+
+
+def ipg_sssp_batch_dev(g: Graph, sources, dist_dev, stream=None):
+    """k SSSP runs into a CUDA tensor of k * n 4-byte entries (row i from sources[i]).
+    Returns supersteps[k]."""
+    lib = load_library()
+    n = ipg_graph_info(g)["n"]
+    src = _sources_arr(sources, n)
+    k = src.size
+    steps = np.zeros(k, dtype=np.uint32)
+    fn = lib.ipg_sssp_batch_dev
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    _check(fn(g.handle, src.ctypes.data if k else None, k, _dev_ptr(dist_dev, 4, k * n, "dist"),
+              steps.ctypes.data if k else None, _stream_ptr(stream)))
+    return steps
+
+
+__all__ += ["ipg_sssp_batch", "ipg_sssp_batch_dev"]

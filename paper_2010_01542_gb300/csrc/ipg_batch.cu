@@ -1,0 +1,397 @@
+// Batched SSSP: many sources on one graph, each an independent synchronous
+// Pregel SSSP (Sec. VI-C), run together superstep by superstep.
+//
+// Sources are processed in groups of 32, one per warp lane.  Values live
+// vertex-major, dist[v][lane], so the 32 sources' values of a vertex are one
+// 128-byte line: in a pull superstep every in-edge (u -> v) costs one coalesced
+// line read of u's sender values for all 32 sources, where 32 separate runs would
+// each pay a random 4-byte gather.  A superstep:
+//   pull     warps walk contiguous chunks of the in-edge lists (CSC).  Lane b keeps
+//            a running min of sval[u][b] + w over the current destination's edges
+//            and flushes it with atomicMin into dist[v][b] when the destination
+//            changes (a row split across chunks is finished by the atomics).  A
+//            lane whose atomicMin lowered the value marks v in cmask[v]; the first
+//            marker appends v to the next frontier (union over the 32 sources).
+//   apply    the previous senders' snapshot rows are reset to kInf, and every
+//            vertex of the next frontier publishes dist[v][b] for the sources
+//            whose value dropped (kInf for the others), which is the snapshot the
+//            next superstep reads; per-source message counts (sum of the senders'
+//            out-degrees) come out of the same pass.
+// Senders therefore send the value they had at the start of the superstep, as in
+// the synchronous model, and every source's distances and superstep count equal
+// those of a standalone ipg_sssp run.
+#include "ipg_internal.cuh"
+
+namespace ipg {
+namespace {
+
+constexpr int kLanes = 32;
+constexpr uint32_t kChunk = 256;  // in-edges per warp task
+constexpr int kUnroll = 4;         // sender lines in flight per warp
+
+struct BatchCounters {
+    unsigned long long msgs[kLanes];  // messages the next superstep's senders send, per source
+    unsigned int next_size;
+    unsigned int status;
+    unsigned int pad[14];
+};
+
+__global__ void chunk_rows_kernel(const uint64_t* __restrict__ off, uint32_t n, uint64_t m, uint64_t chunks,
+                                  uint32_t* __restrict__ chunk_row) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += stride) {
+        // row holding edge c * kChunk: the last row whose start is <= that edge
+        const uint64_t e = c * kChunk;
+        uint32_t lo = 0, hi = n;  // answer in [0, n - 1]
+        while (lo + 1 < hi) {
+            const uint32_t mid = (uint32_t)(((uint64_t)lo + hi) >> 1);
+            if (off[mid] <= e)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        // skip rows that end at or before e (empty rows sharing the offset)
+        while (lo + 1 < n && off[lo + 1] <= e) ++lo;
+        chunk_row[c] = lo;
+    }
+}
+
+__global__ void batch_seed_kernel(const uint32_t* __restrict__ src_int, uint32_t k, const uint64_t* __restrict__ off,
+                                  uint32_t* __restrict__ dist, uint32_t* __restrict__ sval,
+                                  uint32_t* __restrict__ smask, uint32_t* __restrict__ frontier,
+                                  BatchCounters* __restrict__ ctr) {
+    const uint32_t b = threadIdx.x;
+    if (b < k) {
+        const uint32_t v = src_int[b];
+        dist[(uint64_t)v * kLanes + b] = 0;
+        sval[(uint64_t)v * kLanes + b] = 0;
+        const unsigned old = atomicOr(&smask[v], 1u << b);
+        if (old == 0) frontier[atomicAdd(&ctr->next_size, 1u)] = v;
+        ctr->msgs[b] = off[v + 1] - off[v];
+    }
+}
+
+__device__ __forceinline__ void batch_flush(uint32_t v, uint32_t run, uint32_t lane, uint32_t* __restrict__ dist,
+                                            uint32_t* __restrict__ cmask, uint32_t* __restrict__ next,
+                                            BatchCounters* __restrict__ ctr) {
+    bool changed = false;
+    if (run != kInf) {
+        const uint32_t old = atomicMin(&dist[(uint64_t)v * kLanes + lane], run);
+        changed = run < old;
+    }
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, changed);
+    if (mask && lane == 0) {
+        const unsigned old = atomicOr(&cmask[v], mask);
+        if (old == 0) next[atomicAdd(&ctr->next_size, 1u)] = v;
+    }
+}
+
+template <int kWeightKind>
+__global__ void __launch_bounds__(256) batch_pull_kernel(
+    const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ csc_src, const uint8_t* __restrict__ w8,
+    const uint32_t* __restrict__ w32, const uint32_t* __restrict__ chunk_row, uint64_t chunks, uint32_t n, uint64_t m,
+    const uint32_t* __restrict__ sval, const uint32_t* __restrict__ smask, uint32_t* __restrict__ dist,
+    uint32_t* __restrict__ cmask, uint32_t* __restrict__ next, BatchCounters* __restrict__ ctr) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = warp; c < chunks; c += nwarps) {
+        const uint64_t e_begin = c * kChunk;
+        const uint32_t len = (uint32_t)(e_begin + kChunk < m ? kChunk : m - e_begin);
+        uint32_t row = chunk_row[c];
+        uint32_t bound = (uint32_t)(csc_off[row + 1] - e_begin);  // row end, relative to the chunk (may exceed len)
+        uint32_t run = kInf;
+        bool pending = false;  // some lane folded a message into run (warp-uniform)
+        for (uint32_t j0 = 0; j0 < len; j0 += 32) {
+            const uint32_t jl = j0 + lane;
+            uint32_t u_l = 0, w_l = 1, sm_l = 0;
+            if (jl < len) {
+                u_l = __ldcs(csc_src + e_begin + jl);
+                sm_l = __ldg(smask + u_l);
+                if (kWeightKind == 1) w_l = __ldcs(w8 + e_begin + jl);
+                if (kWeightKind == 2) w_l = __ldcs(w32 + e_begin + jl);
+            }
+            // only in-edges whose source sends for some lane of the group
+            unsigned active = __ballot_sync(0xFFFFFFFFu, sm_l != 0);
+            while (active) {
+                int jj[kUnroll];
+                uint32_t s[kUnroll], w[kUnroll];
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) {
+                    jj[q] = active ? __ffs(active) - 1 : -1;
+                    if (active) active &= active - 1;
+                    const int src_lane = jj[q] < 0 ? 0 : jj[q];
+                    const uint32_t u = __shfl_sync(0xFFFFFFFFu, u_l, src_lane);
+                    w[q] = __shfl_sync(0xFFFFFFFFu, w_l, src_lane);
+                    s[q] = jj[q] >= 0 ? __ldg(sval + (uint64_t)u * kLanes + lane) : kInf;  // one 128-byte line
+                }
+#pragma unroll
+                for (int q = 0; q < kUnroll; ++q) {
+                    if (jj[q] >= 0) {
+                        const uint32_t e = j0 + (uint32_t)jj[q];
+                        if (e >= bound) {  // the destination changed (warp-uniform)
+                            if (pending) batch_flush(row, run, lane, dist, cmask, next, ctr);
+                            run = kInf;
+                            pending = false;
+                            do {
+                                ++row;
+                                bound = (uint32_t)(csc_off[row + 1] - e_begin);
+                            } while (e >= bound);
+                        }
+                        if (s[q] != kInf) {
+                            unsigned long long d = (unsigned long long)s[q] + w[q];
+                            if (d >= kInf) {
+                                atomicOr(&ctr->status, kStatusOverflow);
+                                d = kInf - 1;
+                            }
+                            run = min(run, (uint32_t)d);
+                        }
+                        pending = true;
+                    }
+                }
+            }
+        }
+        if (pending) batch_flush(row, run, lane, dist, cmask, next, ctr);
+    }
+}
+
+// previous senders: snapshot rows back to kInf
+__global__ void batch_reset_kernel(const uint32_t* __restrict__ F, uint32_t f, uint32_t* __restrict__ sval,
+                                   uint32_t* __restrict__ smask) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i = warp; i < f; i += nwarps) {
+        const uint32_t u = F[i];
+        sval[(uint64_t)u * kLanes + lane] = kInf;
+        if (lane == 0) smask[u] = 0;
+    }
+}
+
+// next senders: publish their new values, count their messages per source
+__global__ void batch_apply_kernel(const uint32_t* __restrict__ F, uint32_t f, const uint64_t* __restrict__ off,
+                                   const uint32_t* __restrict__ dist, uint32_t* __restrict__ sval,
+                                   uint32_t* __restrict__ smask, uint32_t* __restrict__ cmask,
+                                   BatchCounters* __restrict__ ctr) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long msgs = 0;
+    for (uint64_t i = warp; i < f; i += nwarps) {
+        const uint32_t v = F[i];
+        const uint32_t mask = cmask[v];
+        const bool mine = (mask >> lane) & 1u;
+        sval[(uint64_t)v * kLanes + lane] = mine ? dist[(uint64_t)v * kLanes + lane] : kInf;
+        if (mine) msgs += off[v + 1] - off[v];
+        __syncwarp();
+        if (lane == 0) {
+            smask[v] = mask;
+            cmask[v] = 0;
+        }
+    }
+    if (msgs) atomicAdd(&ctr->msgs[lane], msgs);
+}
+
+// out[b][v] = dist[inv[v]][b] for b < k, through a shared-memory transpose
+__global__ void batch_output_kernel(const uint32_t* __restrict__ dist, const uint32_t* __restrict__ inv, uint32_t n,
+                                    uint32_t k, uint32_t* __restrict__ out, uint64_t out_stride) {
+    __shared__ uint32_t tile[32][33];
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 32 warps
+    for (uint64_t v0 = (uint64_t)blockIdx.x * 32; v0 < n; v0 += (uint64_t)gridDim.x * 32) {
+        const uint64_t v = v0 + w;
+        tile[w][lane] = v < n ? dist[(uint64_t)inv[v] * kLanes + lane] : kInf;
+        __syncthreads();
+        const uint64_t vv = v0 + lane;
+        if (w < k && vv < n) out[(uint64_t)w * out_stride + vv] = tile[lane][w];
+        __syncthreads();
+    }
+}
+
+unsigned grid_for_warps(uint64_t warps, int sms) {
+    uint64_t blocks = (warps + 7) / 8;
+    const uint64_t cap = (uint64_t)sms * 16;
+    if (blocks < 1) blocks = 1;
+    return (unsigned)(blocks < cap ? blocks : cap);
+}
+
+}  // namespace
+
+// Batch workspace lives with the graph; allocated on first use.
+struct BatchWorkspace {
+    uint32_t* dist = nullptr;   // [n][32]
+    uint32_t* sval = nullptr;   // [n][32]
+    uint32_t* smask = nullptr;  // [n]
+    uint32_t* cmask = nullptr;  // [n]
+    uint32_t* fr[2] = {nullptr, nullptr};
+    uint32_t* chunk_row = nullptr;
+    uint64_t chunks = 0;
+    uint32_t* src_int = nullptr;  // [32]
+    BatchCounters* ctr = nullptr;
+    BatchCounters* h_ctr = nullptr;
+};
+
+void batch_free(ipg_graph* g) {
+    BatchWorkspace* b = (BatchWorkspace*)g->batch;
+    if (!b) return;
+    cudaFree(b->dist);
+    cudaFree(b->sval);
+    cudaFree(b->smask);
+    cudaFree(b->cmask);
+    cudaFree(b->fr[0]);
+    cudaFree(b->fr[1]);
+    cudaFree(b->chunk_row);
+    cudaFree(b->src_int);
+    cudaFree(b->ctr);
+    if (b->h_ctr) cudaFreeHost(b->h_ctr);
+    delete b;
+    g->batch = nullptr;
+}
+
+static ipg_status batch_prepare(ipg_graph* g, cudaStream_t st) {
+    IPG_TRY(ensure_csc(g, st));
+    if (g->batch) return IPG_OK;
+    BatchWorkspace* b = new BatchWorkspace();
+    g->batch = b;
+    const uint32_t n = g->n;
+    IPG_CUDA(cudaMalloc(&b->dist, sizeof(uint32_t) * kLanes * (size_t)n));
+    IPG_CUDA(cudaMalloc(&b->sval, sizeof(uint32_t) * kLanes * (size_t)n));
+    IPG_CUDA(cudaMalloc(&b->smask, sizeof(uint32_t) * (size_t)n));
+    IPG_CUDA(cudaMalloc(&b->cmask, sizeof(uint32_t) * (size_t)n));
+    IPG_CUDA(cudaMalloc(&b->fr[0], sizeof(uint32_t) * (size_t)n));
+    IPG_CUDA(cudaMalloc(&b->fr[1], sizeof(uint32_t) * (size_t)n));
+    IPG_CUDA(cudaMalloc(&b->src_int, sizeof(uint32_t) * kLanes));
+    IPG_CUDA(cudaMalloc(&b->ctr, sizeof(BatchCounters)));
+    IPG_CUDA(cudaHostAlloc(&b->h_ctr, sizeof(BatchCounters), cudaHostAllocDefault));
+    b->chunks = (g->m + kChunk - 1) / kChunk;
+    IPG_CUDA(cudaMalloc(&b->chunk_row, sizeof(uint32_t) * (b->chunks ? b->chunks : 1)));
+    if (b->chunks) {
+        chunk_rows_kernel<<<grid_for_warps(b->chunks / 32 + 1, sm_count_of(g->device)), 256, 0, st>>>(
+            g->csc_off, n, g->m, b->chunks, b->chunk_row);
+        IPG_CUDA(cudaGetLastError());
+    }
+    return IPG_OK;
+}
+
+// one group of k <= 32 sources (caller ids) -> out rows [0, k), row stride out_stride
+static ipg_status batch_group(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* out, uint64_t out_stride,
+                              uint32_t* supersteps, cudaStream_t st) {
+    BatchWorkspace* b = (BatchWorkspace*)g->batch;
+    const uint32_t n = g->n;
+    const int sms = sm_count_of(g->device);
+    // caller ids -> internal ids (inv is device-resident)
+    uint32_t h_src[kLanes];
+    for (uint32_t i = 0; i < k; ++i) h_src[i] = sources[i];
+    IPG_CUDA(cudaMemcpyAsync(b->src_int, h_src, sizeof(uint32_t) * k, cudaMemcpyHostToDevice, st));
+    IPG_CUDA(cudaMemsetAsync(b->dist, 0xFF, sizeof(uint32_t) * kLanes * (size_t)n, st));
+    IPG_CUDA(cudaMemsetAsync(b->sval, 0xFF, sizeof(uint32_t) * kLanes * (size_t)n, st));
+    IPG_CUDA(cudaMemsetAsync(b->ctr, 0, sizeof(BatchCounters), st));
+    IPG_CUDA(cudaMemsetAsync(b->smask, 0, sizeof(uint32_t) * (size_t)n, st));
+    IPG_CUDA(cudaMemsetAsync(b->cmask, 0, sizeof(uint32_t) * (size_t)n, st));
+    IPG_TRY(map_to_internal(g, b->src_int, k, st));
+    batch_seed_kernel<<<1, kLanes, 0, st>>>(b->src_int, k, g->off, b->dist, b->sval, b->smask, b->fr[0], b->ctr);
+    IPG_CUDA(cudaGetLastError());
+    IPG_CUDA(cudaMemcpyAsync(b->h_ctr, b->ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, st));
+    IPG_CUDA(cudaStreamSynchronize(st));
+    uint32_t count[kLanes];
+    for (uint32_t i = 0; i < k; ++i) count[i] = 1 + (b->h_ctr->msgs[i] > 0 ? 1 : 0);
+    uint32_t f = b->h_ctr->next_size;
+    int cur = 0;
+    for (uint32_t s = 0; f > 0; ++s) {
+        IPG_CUDA(cudaMemsetAsync(b->ctr, 0, sizeof(BatchCounters), st));
+        const unsigned grid = grid_for_warps(b->chunks, sms);
+        if (g->csc_w8)
+            batch_pull_kernel<1><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,
+                                                       b->chunks, n, g->m, b->sval, b->smask, b->dist, b->cmask,
+                                                       b->fr[cur ^ 1], b->ctr);
+        else if (g->csc_w)
+            batch_pull_kernel<2><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,
+                                                       b->chunks, n, g->m, b->sval, b->smask, b->dist, b->cmask,
+                                                       b->fr[cur ^ 1], b->ctr);
+        else
+            batch_pull_kernel<0><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,
+                                                       b->chunks, n, g->m, b->sval, b->smask, b->dist, b->cmask,
+                                                       b->fr[cur ^ 1], b->ctr);
+        IPG_CUDA(cudaGetLastError());
+        batch_reset_kernel<<<grid_for_warps(f, sms), 256, 0, st>>>(b->fr[cur], f, b->sval, b->smask);
+        IPG_CUDA(cudaGetLastError());
+        IPG_CUDA(cudaMemcpyAsync(&b->h_ctr->next_size, &b->ctr->next_size, sizeof(unsigned),
+                                 cudaMemcpyDeviceToHost, st));
+        IPG_CUDA(cudaStreamSynchronize(st));
+        const uint32_t fn = b->h_ctr->next_size;
+        if (fn > n) return set_error(IPG_EDEVICE, "ipg_sssp_batch: frontier overflow");
+        if (fn) {
+            batch_apply_kernel<<<grid_for_warps(fn, sms), 256, 0, st>>>(b->fr[cur ^ 1], fn, g->off, b->dist, b->sval,
+                                                                      b->smask, b->cmask, b->ctr);
+            IPG_CUDA(cudaGetLastError());
+        }
+        IPG_CUDA(cudaMemcpyAsync(b->h_ctr, b->ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, st));
+        IPG_CUDA(cudaStreamSynchronize(st));
+        if (b->h_ctr->status & kStatusOverflow) return set_error(IPG_EOVERFLOW, "ipg_sssp_batch: a path length reached UINT32_MAX");
+        for (uint32_t i = 0; i < k; ++i) count[i] += b->h_ctr->msgs[i] > 0 ? 1 : 0;
+        f = fn;
+        cur ^= 1;
+    }
+    batch_output_kernel<<<grid_for_warps((uint64_t)n, sms), 1024, 0, st>>>(b->dist, g->inv, n, k, out, out_stride);
+    IPG_CUDA(cudaGetLastError());
+    IPG_CUDA(cudaStreamSynchronize(st));
+    if (supersteps)
+        for (uint32_t i = 0; i < k; ++i) supersteps[i] = count[i];
+    return IPG_OK;
+}
+
+ipg_status sssp_batch_run(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_dev,
+                          uint32_t* supersteps_out, cudaStream_t st) {
+    if (!g) return set_error(IPG_EINVAL, "ipg_sssp_batch: graph is NULL");
+    if (k == 0) return IPG_OK;
+    if (!sources || !dist_dev) return set_error(IPG_EINVAL, "ipg_sssp_batch: NULL argument");
+    for (uint32_t i = 0; i < k; ++i)
+        if (sources[i] >= g->n)
+            return set_error(IPG_EINVAL, "ipg_sssp_batch: source %u (index %u) >= n = %u", sources[i], i, g->n);
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return set_error(IPG_ECUDA, "ipg_sssp_batch: cannot select the graph's device");
+    IPG_TRY(batch_prepare(g, st));
+    for (uint32_t i0 = 0; i0 < k; i0 += kLanes) {
+        const uint32_t kk = k - i0 < (uint32_t)kLanes ? k - i0 : (uint32_t)kLanes;
+        IPG_TRY(batch_group(g, sources + i0, kk, dist_dev + (uint64_t)i0 * g->n, g->n,
+                            supersteps_out ? supersteps_out + i0 : nullptr, st));
+    }
+    return IPG_OK;
+}
+
+}  // namespace ipg
+
+using namespace ipg;
+
+extern "C" {
+
+ipg_status ipg_sssp_batch_dev(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_dev,
+                              uint32_t* supersteps_out, void* stream) {
+    return sssp_batch_run(g, sources, k, dist_dev, supersteps_out, (cudaStream_t)stream);
+}
+
+// host output: groups of 32 sources through a 32 x n device staging buffer
+ipg_status ipg_sssp_batch(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_out,
+                          uint32_t* supersteps_out) {
+    if (!g) return set_error(IPG_EINVAL, "ipg_sssp_batch: graph is NULL");
+    if (k && (!sources || !dist_out)) return set_error(IPG_EINVAL, "ipg_sssp_batch: NULL argument");
+    DeviceGuard guard(g->device);
+    const uint64_t n = g->n;
+    uint32_t* stage = nullptr;
+    const uint32_t group = k < 32 ? k : 32;
+    if (k) IPG_CUDA(cudaMalloc(&stage, sizeof(uint32_t) * group * (n ? n : 1)));
+    ipg_status rc = IPG_OK;
+    for (uint32_t i0 = 0; i0 < k && rc == IPG_OK; i0 += 32) {
+        const uint32_t kk = k - i0 < 32 ? k - i0 : 32;
+        rc = sssp_batch_run(g, sources + i0, kk, stage, supersteps_out ? supersteps_out + i0 : nullptr, g->stream);
+        if (rc == IPG_OK && n) {
+            cudaError_t e = cudaMemcpyAsync(dist_out + (uint64_t)i0 * n, stage, sizeof(uint32_t) * kk * n,
+                                            cudaMemcpyDeviceToHost, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+            if (e != cudaSuccess) rc = cuda_fail(e, "copy of batched distances", __FILE__, __LINE__);
+        }
+    }
+    if (stage) cudaFree(stage);
+    return rc;
+}
+
+}  // extern "C"

@@ -441,6 +441,17 @@ done:
 
 int sm_count_of(int dev) { return device_sms(dev); }
 
+__global__ void map_ids_kernel(const uint32_t* __restrict__ inv, uint32_t* __restrict__ ids, uint32_t k) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) ids[i] = inv[ids[i]];
+}
+
+ipg_status map_to_internal(ipg_graph* g, uint32_t* ids, uint32_t k, cudaStream_t st) {
+    if (!k) return IPG_OK;
+    map_ids_kernel<<<(k + 255) / 256, 256, 0, st>>>(g->inv, ids, k);
+    IPG_CUDA(cudaGetLastError());
+    return IPG_OK;
+}
+
 Tuning& tuning() {
     static Tuning t;
     return t;
@@ -488,6 +499,7 @@ static void free_graph(ipg_graph* g) {
     f(g->push_tile_row);
     f(g->val_stage);
     f(g->counters);
+    batch_free(g);
     if (g->h_counters) cudaFreeHost(g->h_counters);
     g->timer.destroy();
     if (g->stream) cudaStreamDestroy(g->stream);

@@ -127,6 +127,8 @@ struct ipg_graph {
     ipg::PushCounters* counters = nullptr;    // device
     ipg::PushCounters* h_counters = nullptr;  // pinned host mirror
 
+    void* batch = nullptr;          // batched-SSSP workspace (ipg_batch.cu)
+
     cudaStream_t stream = nullptr;  // used by the host-buffer entry points
     ipg::StepTimer timer;
 };
@@ -138,6 +140,12 @@ ipg_status ensure_pull_partition(ipg_graph* g, cudaStream_t st);
 ipg_status count_in_nonempty(ipg_graph* g, cudaStream_t st);
 ipg_status ensure_push_workspace(ipg_graph* g, bool receivers);
 int sm_count_of(int dev);
+// in ipg_batch.cu
+void batch_free(ipg_graph* g);
+ipg_status sssp_batch_run(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_dev,
+                          uint32_t* supersteps_out, cudaStream_t st);
+// caller ids -> internal ids, in place on the device
+ipg_status map_to_internal(ipg_graph* g, uint32_t* ids, uint32_t k, cudaStream_t st);
 // in ipg_pull_min.cu
 ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, const uint32_t* F, const uint32_t* fval, uint32_t f,
                               uint32_t* val, uint32_t* next, cudaStream_t st, cudaEvent_t ev_kernel);

@@ -1,0 +1,94 @@
+"""Batched SSSP (ipg_sssp_batch): every row equals a standalone ipg_sssp run from the
+same source — distances and superstep count, bit for bit — and the oracle on small
+graphs.  Groups of 32 sources share supersteps, so the cases cover groups that end
+early or late, more than 32 sources, repeated sources and sources without out-edges."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ipg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2010_01542_gb300 as ipg
+    from paper_2010_01542_gb300 import _build
+
+    _build.build()
+    ipg.load_library()
+    return ipg
+
+
+def _check_batch(ipg, g, sources, weights, use_oracle=False):
+    h = ipg.ipg_graph_create(g.offsets, g.cols, weights, g.n, g.m, g.directed)
+    dist, steps = ipg.ipg_sssp_batch(h, sources)
+    assert dist.shape == (len(sources), g.n)
+    for i, s in enumerate(sources):
+        ref, cnt, _ = ipg.ipg_sssp(h, int(s))
+        np.testing.assert_array_equal(dist[i], ref, err_msg=f"source {s}")
+        assert steps[i] == cnt, (s, steps[i], cnt)
+        if use_oracle:
+            o = oracle.sssp(g.n, g.offsets, g.cols, weights, int(s))
+            np.testing.assert_array_equal(dist[i], o.values)
+            assert steps[i] == o.supersteps
+    return dist, steps
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_batch_random_multigraphs(ipg, seed):
+    rng = np.random.default_rng(50 + seed)
+    n = int(rng.integers(2, 2500))
+    g = gen.random_multigraph(n, int(rng.integers(1, 20000)), seed=seed, weighted=True)
+    k = int(rng.integers(1, 70))
+    sources = rng.integers(0, n, size=k)
+    _check_batch(ipg, g, sources, g.weights, use_oracle=True)
+    _check_batch(ipg, g, sources, None, use_oracle=True)
+
+
+@pytest.mark.parametrize("scale", [8, 12, 16])
+def test_batch_rmat(ipg, scale):
+    g = gen.rmat(scale, 16, seed=scale, weighted=True)
+    rng = np.random.default_rng(scale)
+    sources = list(rng.integers(0, g.n, size=40)) + [gen.max_out_degree_vertex(g)] * 2
+    zero_out = np.nonzero(g.out_degree() == 0)[0]
+    if zero_out.size:
+        sources.append(int(zero_out[0]))
+    _check_batch(ipg, g, np.array(sources), g.weights, use_oracle=scale <= 12)
+
+
+def test_batch_wide_weights_and_undirected(ipg):
+    g = gen.rmat(11, 8, seed=3)
+    rng = np.random.default_rng(3)
+    w = rng.integers(1, 100000, size=g.m).astype(np.uint32)  # u32 weights (> 255)
+    _check_batch(ipg, g, rng.integers(0, g.n, size=33), w, use_oracle=True)
+    u = gen.rmat(11, 8, seed=4, undirected=True, weighted=True)
+    _check_batch(ipg, u, rng.integers(0, u.n, size=17), u.weights, use_oracle=True)
+
+
+def test_batch_device_entry_and_errors(ipg):
+    import torch
+
+    g = gen.rmat(10, 16, seed=5, weighted=True)
+    h = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, True)
+    sources = np.arange(0, 40, dtype=np.uint32)
+    ref, ref_steps = ipg.ipg_sssp_batch(h, sources)
+    d = torch.empty(len(sources) * g.n, dtype=torch.int32, device="cuda")
+    steps = ipg.ipg_sssp_batch_dev(h, sources, d)
+    np.testing.assert_array_equal(d.cpu().numpy().view(np.uint32).reshape(len(sources), g.n), ref)
+    np.testing.assert_array_equal(steps, ref_steps)
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_sssp_batch(h, [0, g.n])
+    assert e.value.status == 1
+    big = gen.csr_from_edges(3, [0, 1], [1, 2], [0xFFFFFF00, 0xFFFFFF00])
+    hb = ipg.ipg_graph_create(big.offsets, big.cols, big.weights, 3, 2, True)
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_sssp_batch(hb, [0])
+    assert e.value.status == 7
+    dist, steps = ipg.ipg_sssp_batch(h, [])
+    assert dist.shape == (0, g.n)
