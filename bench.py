@@ -45,8 +45,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["billion", "batch"], default="billion",
-                   help="billion: the default bench line; batch: 256-source batched SSSP vs one at a time")
+    p.add_argument("--workload", choices=["billion", "batch", "cc-batch"], default="billion",
+                   help="billion: the default bench line; batch: 256-source batched SSSP vs one at a time; "
+                        "cc-batch: 64 uneven Hashmin graphs in one object vs one at a time")
     p.add_argument("--batch-sources", type=int, default=256)
     p.add_argument("--scale", type=int, default=26)
     p.add_argument("--edge-factor", type=int, default=28)
@@ -497,12 +498,79 @@ def run_batch(a):
     h.destroy()
 
 
+def cc_batch_scales(count, seed):
+    """scale_i = 10 + splitmix64(splitmix64(seed) + i) % 11: uneven graphs of 2^10 .. 2^20 vertices."""
+    import gen
+
+    base = gen.splitmix64(seed)
+    return [10 + gen.splitmix64((base + i) & 0xFFFFFFFFFFFFFFFF) % 11 for i in range(count)]
+
+
+def run_cc_batch(a, count=64):
+    """Hashmin on 64 undirected R-MAT graphs (EF 16, uneven scales 10..20, seeds 1..64) held in
+    one batch graph, one ipg_hashmin_cc_batch_dev call per step, against 64 separate graphs run
+    one at a time with ipg_hashmin_cc_dev; labels and superstep counts compared."""
+    import torch
+
+    import gen
+    import paper_2010_01542_gb300 as ipg
+
+    world, rank, local = dist_init(a)
+    ipg.load_library()
+    scales = cc_batch_scales(count, a.seed)
+    graphs = [gen.rmat_device(sc, 16, seed=i + 1, undirected=True, device=local).to_host()
+              for i, sc in enumerate(scales)]
+    hb = ipg.ipg_graph_create_batch(graphs, directed=False)
+    _, bases = ipg.ipg_graph_instances(hb)
+    total_n = int(bases[-1])
+    total_m = sum(g.m for g in graphs)
+    stream = torch.cuda.Stream()
+    labels = torch.empty(total_n, dtype=torch.int32, device="cuda")
+    for _ in range(max(a.warmup, 1)):
+        steps_b = ipg.ipg_hashmin_cc_batch_dev(hb, labels, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(a.steps):
+        steps_b = ipg.ipg_hashmin_cc_batch_dev(hb, labels, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = all_max(e0.elapsed_time(e1) / a.steps, world)
+    singles = [ipg.ipg_graph_create(g.offsets, g.cols, None, g.n, g.m, False) for g in graphs]
+    outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    for h, o in zip(singles, outs):
+        ipg.ipg_hashmin_cc_dev(h, o, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    counts = [ipg.ipg_hashmin_cc_dev(h, o, stream=stream)[0] for h, o in zip(singles, outs)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_single = all_max(e0.elapsed_time(e1), world)
+    equal = all(bool(torch.equal(labels[int(bases[i]):int(bases[i + 1])], outs[i])) and counts[i] == int(steps_b[i])
+                for i in range(count))
+    if rank == 0:
+        line = {"metric": "Hashmin CC graphs/s, many graphs in one batch vs one at a time", "unit": "graphs/s",
+                "value": round(world * count / (t_batch / 1e3), 1), "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": round(t_batch, 3), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": f"{count} undirected R-MAT graphs, EF 16, scales 10..20 "
+                                       f"(scale_i from splitmix64, seed {a.seed}), graph seeds 1..{count}",
+                           "scales": scales, "total_n": total_n, "total_m": total_m},
+                "one_at_a_time": {"value": round(world * count / (t_single / 1e3), 1), "unit": "graphs/s",
+                                  "ms_total": round(t_single, 2)},
+                "speedup": round(t_single / t_batch, 2), "results_equal": equal,
+                "gteps": round(sum(int(x) for x in [total_m]) / (t_batch / 1e3) / 1e9, 2)}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batch":
         run_batch(a)
+    elif a.workload == "cc-batch":
+        run_cc_batch(a)
     else:
         run_ours(a)
 

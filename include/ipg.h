@@ -106,6 +106,24 @@ ipg_status ipg_graph_create_dev(const uint64_t* offsets_dev, const uint32_t* col
                                 const uint32_t* weights_dev, uint32_t n, uint64_t m, int directed, void* stream,
                                 ipg_graph** out);
 
+/*
+ * ipg_graph_create_batch — one graph object holding `count` independent
+ * graphs (instances) side by side, so one call runs a Pregel program on all of
+ * them together (batched queries on many small graphs; not in the paper).
+ *   offsets[i], columns[i], weights[i] (or weights = NULL), n[i], m[i]: host CSR
+ *   of instance i, as for ipg_graph_create (columns < n[i]); weights for all
+ *   instances or for none;  directed: applies to every instance.
+ * Instance i's vertex v is vertex base_i + v of the batch graph, with
+ * base_i = n[0] + ... + n[i-1]; per-vertex outputs follow that layout.
+ */
+ipg_status ipg_graph_create_batch(uint32_t count, const uint64_t* const* offsets, const uint32_t* const* columns,
+                                  const uint32_t* const* weights, const uint32_t* n, const uint64_t* m, int directed,
+                                  ipg_graph** out);
+
+/* Number of instances (1 for a plain graph) and, if bases is not NULL, the
+ * count + 1 instance bases (bases[count] = total n). */
+ipg_status ipg_graph_instances(const ipg_graph* g, uint32_t* count, uint32_t* bases);
+
 /* Free the graph and all device memory it owns.  NULL is ignored. */
 void ipg_graph_destroy(ipg_graph* g);
 
@@ -133,6 +151,16 @@ ipg_status ipg_pagerank_dev(ipg_graph* g, uint32_t updates, float* ranks_dev, ip
  */
 ipg_status ipg_hashmin_cc(ipg_graph* g, uint32_t* labels_out, ipg_stats* stats);
 ipg_status ipg_hashmin_cc_dev(ipg_graph* g, uint32_t* labels_dev, ipg_stats* stats, void* stream);
+
+/*
+ * ipg_hashmin_cc_batch — Hashmin on every instance of a batch graph at once.
+ *   labels_out      host, total n uint32: instance i's labels at [base_i, base_i + n_i),
+ *                   as instance-local ids (equal to ipg_hashmin_cc on that instance alone);
+ *   supersteps_out  host, one entry per instance or NULL: each instance's superstep count.
+ * ipg_hashmin_cc_batch_dev writes the labels to device memory on `stream`.
+ */
+ipg_status ipg_hashmin_cc_batch(ipg_graph* g, uint32_t* labels_out, uint32_t* supersteps_out);
+ipg_status ipg_hashmin_cc_batch_dev(ipg_graph* g, uint32_t* labels_dev, uint32_t* supersteps_out, void* stream);
 
 /*
  * ipg_sssp — single-source shortest paths (Sec. VI-C, SSSP) with a min

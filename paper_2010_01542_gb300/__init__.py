@@ -369,3 +369,79 @@ def ipg_sssp_batch_dev(g: Graph, sources, dist_dev, stream=None):
 
 
 __all__ += ["ipg_sssp_batch", "ipg_sssp_batch_dev"]
+
+
+def ipg_graph_create_batch(graphs, directed: bool) -> Graph:
+    """One graph object holding several independent host CSR graphs (objects with n,
+    offsets, cols and optional weights).  Instance i's vertices follow instance i-1's."""
+    lib = load_library()
+    count = len(graphs)
+    keep = []
+    P64, P32 = ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint32)
+    offs = (P64 * count)()
+    cols = (P32 * count)()
+    ws = (P32 * count)()
+    ns = (ctypes.c_uint32 * count)()
+    ms = (ctypes.c_uint64 * count)()
+    weighted = count > 0 and all(getattr(gr, "weights", None) is not None for gr in graphs)
+    for i, gr in enumerate(graphs):
+        o = np.ascontiguousarray(gr.offsets, dtype=np.uint64)
+        c = np.ascontiguousarray(gr.cols, dtype=np.uint32)
+        keep += [o, c]
+        offs[i] = o.ctypes.data_as(P64)
+        cols[i] = c.ctypes.data_as(P32) if c.size else P32()
+        if weighted:
+            w = np.ascontiguousarray(gr.weights, dtype=np.uint32)
+            keep.append(w)
+            ws[i] = w.ctypes.data_as(P32) if w.size else P32()
+        ns[i] = int(gr.n)
+        ms[i] = int(o[-1])
+    fn = lib.ipg_graph_create_batch
+    fn.argtypes = [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+    fn.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    _check(fn(count, offs, cols, ws if weighted else None, ns, ms, int(bool(directed)), ctypes.byref(h)))
+    return Graph(h)
+
+
+def ipg_graph_instances(g: Graph):
+    """(count, bases[count + 1])"""
+    lib = load_library()
+    fn = lib.ipg_graph_instances
+    fn.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    c = ctypes.c_uint32()
+    _check(fn(g.handle, ctypes.byref(c), None))
+    bases = np.zeros(c.value + 1, dtype=np.uint32)
+    _check(fn(g.handle, ctypes.byref(c), bases.ctypes.data))
+    return int(c.value), bases
+
+
+def ipg_hashmin_cc_batch(g: Graph, labels_out: Optional[np.ndarray] = None):
+    """Hashmin on every instance.  Returns (labels[total n] instance-local, supersteps[count])."""
+    lib = load_library()
+    n = ipg_graph_info(g)["n"]
+    count, _ = ipg_graph_instances(g)
+    out = np.empty(n, dtype=np.uint32) if labels_out is None else labels_out
+    steps = np.zeros(count, dtype=np.uint32)
+    fn = lib.ipg_hashmin_cc_batch
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    _check(fn(g.handle, out.ctypes.data if n else None, steps.ctypes.data))
+    return out, steps
+
+
+def ipg_hashmin_cc_batch_dev(g: Graph, labels_dev, stream=None):
+    lib = load_library()
+    n = ipg_graph_info(g)["n"]
+    count, _ = ipg_graph_instances(g)
+    steps = np.zeros(count, dtype=np.uint32)
+    fn = lib.ipg_hashmin_cc_batch_dev
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    _check(fn(g.handle, _dev_ptr(labels_dev, 4, n, "labels"), steps.ctypes.data, _stream_ptr(stream)))
+    return steps
+
+
+__all__ += ["ipg_graph_create_batch", "ipg_graph_instances", "ipg_hashmin_cc_batch", "ipg_hashmin_cc_batch_dev"]

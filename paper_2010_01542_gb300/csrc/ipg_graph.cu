@@ -499,6 +499,9 @@ static void free_graph(ipg_graph* g) {
     f(g->push_tile_row);
     f(g->val_stage);
     f(g->counters);
+    f(g->inst_base);
+    f(g->inst_msgs);
+    delete[] g->inst_base_host;
     batch_free(g);
     if (g->h_counters) cudaFreeHost(g->h_counters);
     g->timer.destroy();
@@ -581,11 +584,109 @@ static ipg_status create_impl(const uint64_t* offsets, const uint32_t* columns, 
     return IPG_OK;
 }
 
+ipg_status create_graph(const uint64_t* offsets, const uint32_t* columns, const uint32_t* weights, uint32_t n,
+                        uint64_t m, int directed, cudaStream_t user_stream, bool from_device, ipg_graph** out) {
+    return create_impl(offsets, columns, weights, n, m, directed, user_stream, from_device, out);
+}
+
 }  // namespace ipg
 
 using namespace ipg;
 
 extern "C" {
+
+ipg_status ipg_graph_create_batch(uint32_t count, const uint64_t* const* offsets, const uint32_t* const* columns,
+                                  const uint32_t* const* weights, const uint32_t* n, const uint64_t* m, int directed,
+                                  ipg_graph** out) {
+    if (!out) return set_error(IPG_EINVAL, "ipg_graph_create_batch: out is NULL");
+    *out = nullptr;
+    if (count == 0 || !offsets || !n || !m) return set_error(IPG_EINVAL, "ipg_graph_create_batch: empty batch or NULL");
+    uint64_t N = 0, M = 0;
+    bool any_w = false, all_w = true;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (!offsets[i]) return set_error(IPG_EINVAL, "ipg_graph_create_batch: offsets[%u] is NULL", i);
+        if (m[i] && (!columns || !columns[i]))
+            return set_error(IPG_EINVAL, "ipg_graph_create_batch: columns[%u] is NULL", i);
+        if (offsets[i][0] != 0 || offsets[i][n[i]] != m[i])
+            return set_error(IPG_EINVAL, "ipg_graph_create_batch: instance %u: offsets[0] must be 0 and offsets[n] = m", i);
+        const bool w = weights && weights[i];
+        any_w |= w;
+        all_w &= w;
+        N += n[i];
+        M += m[i];
+    }
+    if (any_w && !all_w) return set_error(IPG_EINVAL, "ipg_graph_create_batch: weights for some instances only");
+    if (N > 0xFFFFFFFFull) return set_error(IPG_EINVAL, "ipg_graph_create_batch: more than 2^32 - 1 vertices in total");
+    uint64_t* off = nullptr;
+    uint32_t* col = nullptr;
+    uint32_t* w = nullptr;
+    uint32_t* bases = new (std::nothrow) uint32_t[count + 1];
+    if (cudaMallocHost(&off, sizeof(uint64_t) * (N + 1)) != cudaSuccess ||
+        cudaMallocHost(&col, sizeof(uint32_t) * (M ? M : 1)) != cudaSuccess ||
+        (any_w && cudaMallocHost(&w, sizeof(uint32_t) * (M ? M : 1)) != cudaSuccess) || !bases) {
+        if (off) cudaFreeHost(off);
+        if (col) cudaFreeHost(col);
+        if (w) cudaFreeHost(w);
+        delete[] bases;
+        return set_error(IPG_ENOMEM, "ipg_graph_create_batch: pinned staging allocation failed");
+    }
+    // the disjoint union: instance i's vertex v is vertex base_i + v, its edges follow
+    uint64_t vb = 0, eb = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        bases[i] = (uint32_t)vb;
+        for (uint32_t v = 0; v < n[i]; ++v) off[vb + v] = eb + offsets[i][v];
+        for (uint64_t e = 0; e < m[i]; ++e) {
+            const uint32_t c = columns[i][e];
+            if (c >= n[i]) {  // would silently land in another instance
+                cudaFreeHost(off);
+                cudaFreeHost(col);
+                if (w) cudaFreeHost(w);
+                delete[] bases;
+                return set_error(IPG_EINVAL, "ipg_graph_create_batch: instance %u has a column >= its n", i);
+            }
+            col[eb + e] = (uint32_t)vb + c;
+        }
+        if (any_w && m[i]) memcpy(w + eb, weights[i], sizeof(uint32_t) * m[i]);
+        vb += n[i];
+        eb += m[i];
+    }
+    off[N] = M;
+    bases[count] = (uint32_t)N;
+    ipg_graph* g = nullptr;
+    ipg_status rc = create_graph(off, col, any_w ? w : nullptr, (uint32_t)N, M, directed, nullptr, false, &g);
+    cudaFreeHost(off);
+    cudaFreeHost(col);
+    if (w) cudaFreeHost(w);
+    if (rc != IPG_OK) {
+        delete[] bases;
+        return rc;
+    }
+    g->instances = count;
+    g->inst_base_host = bases;
+    if (cudaMalloc(&g->inst_base, sizeof(uint32_t) * (count + 1)) != cudaSuccess ||
+        cudaMalloc(&g->inst_msgs, sizeof(unsigned long long) * count) != cudaSuccess ||
+        cudaMemcpy(g->inst_base, bases, sizeof(uint32_t) * (count + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+        free_graph(g);
+        return set_error(IPG_ENOMEM, "ipg_graph_create_batch: instance table allocation failed");
+    }
+    *out = g;
+    return IPG_OK;
+}
+
+ipg_status ipg_graph_instances(const ipg_graph* g, uint32_t* count, uint32_t* bases) {
+    if (!g) return set_error(IPG_EINVAL, "ipg_graph_instances: graph is NULL");
+    const uint32_t c = g->instances ? g->instances : 1;
+    if (count) *count = c;
+    if (bases) {
+        if (g->instances)
+            memcpy(bases, g->inst_base_host, sizeof(uint32_t) * (c + 1));
+        else {
+            bases[0] = 0;
+            bases[1] = g->n;
+        }
+    }
+    return IPG_OK;
+}
 
 ipg_status ipg_graph_create(const uint64_t* offsets, const uint32_t* columns, const uint32_t* weights, uint32_t n,
                             uint64_t m, int directed, ipg_graph** out) {

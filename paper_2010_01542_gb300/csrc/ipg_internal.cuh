@@ -129,6 +129,13 @@ struct ipg_graph {
 
     void* batch = nullptr;          // batched-SSSP workspace (ipg_batch.cu)
 
+    // graphs created by ipg_graph_create_batch: instance i owns caller ids
+    // [inst_base[i], inst_base[i+1])
+    uint32_t instances = 0;
+    uint32_t* inst_base_host = nullptr;  // instances + 1
+    uint32_t* inst_base = nullptr;       // device copy
+    unsigned long long* inst_msgs = nullptr;  // device, per instance
+
     cudaStream_t stream = nullptr;  // used by the host-buffer entry points
     ipg::StepTimer timer;
 };
@@ -140,6 +147,9 @@ ipg_status ensure_pull_partition(ipg_graph* g, cudaStream_t st);
 ipg_status count_in_nonempty(ipg_graph* g, cudaStream_t st);
 ipg_status ensure_push_workspace(ipg_graph* g, bool receivers);
 int sm_count_of(int dev);
+// in ipg_graph.cu: shared by create and create_batch
+ipg_status create_graph(const uint64_t* offsets, const uint32_t* columns, const uint32_t* weights, uint32_t n,
+                        uint64_t m, int directed, cudaStream_t user_stream, bool from_device, ipg_graph** out);
 // in ipg_batch.cu
 void batch_free(ipg_graph* g);
 ipg_status sssp_batch_run(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_dev,

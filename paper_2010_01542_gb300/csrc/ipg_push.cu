@@ -26,6 +26,8 @@
 // during superstep s is sent only in s+1: the run is the synchronous Pregel
 // execution, superstep for superstep, and the per-superstep counts match the
 // model exactly.
+#include <vector>
+
 #include "ipg_internal.cuh"
 
 namespace ipg {
@@ -317,6 +319,53 @@ __global__ void __launch_bounds__(kPushThreads) push_relax_kernel(
     }
 }
 
+// instance of caller id c: the last i with bases[i] <= c (empty instances are skipped)
+__device__ __forceinline__ uint32_t instance_of(const uint32_t* __restrict__ bases, uint32_t count, uint32_t c) {
+    uint32_t lo = 0, hi = count;
+    while (lo + 1 < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (bases[mid] <= c)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// per-instance messages of this superstep: sum of the senders' out-degrees, by instance
+__global__ void instance_msgs_kernel(const uint32_t* __restrict__ F, uint32_t f, const uint64_t* __restrict__ off,
+                                     const uint32_t* __restrict__ perm, const uint32_t* __restrict__ bases,
+                                     uint32_t count, unsigned long long* __restrict__ inst_msgs) {
+    extern __shared__ unsigned long long s_acc[];
+    const bool local = count <= 2048;
+    if (local)
+        for (uint32_t k = threadIdx.x; k < count; k += blockDim.x) s_acc[k] = 0;
+    __syncthreads();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < f; i += stride) {
+        const uint32_t u = F[i];
+        const unsigned long long d = off[u + 1] - off[u];
+        if (!d) continue;
+        const uint32_t inst = instance_of(bases, count, perm[u]);
+        if (local)
+            atomicAdd(&s_acc[inst], d);
+        else
+            atomicAdd(&inst_msgs[inst], d);
+    }
+    __syncthreads();
+    if (local)
+        for (uint32_t k = threadIdx.x; k < count; k += blockDim.x)
+            if (s_acc[k]) atomicAdd(&inst_msgs[k], s_acc[k]);
+}
+
+// labels in caller ids of the union -> instance-local ids
+__global__ void local_labels_kernel(uint32_t* __restrict__ labels, uint32_t n, const uint32_t* __restrict__ bases,
+                                    uint32_t count) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        labels[v] -= bases[instance_of(bases, count, (uint32_t)v)];
+}
+
 unsigned grid_cap(uint64_t work, unsigned cap = 152 * 16) {
     uint64_t b = (work + 255) / 256;
     if (b < 1) b = 1;
@@ -379,7 +428,8 @@ ipg_status ensure_events_push(size_t count, cudaEvent_t** evs) {
     return IPG_OK;
 }
 
-ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_stats* stats, cudaStream_t st) {
+ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_stats* stats, cudaStream_t st,
+                    uint32_t* inst_supersteps = nullptr) {
     stats_begin(stats);
     const char* name = kind == kHashmin ? "ipg_hashmin_cc" : "ipg_sssp";
     if (!g) return set_error(IPG_EINVAL, "%s: graph is NULL", name);
@@ -426,6 +476,11 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
     uint32_t s = 0;
     uint64_t prev_receivers = 0;
     uint32_t count = 0;
+    const uint32_t ninst = g->instances;
+    const bool per_inst = inst_supersteps && ninst;
+    std::vector<unsigned long long> h_inst(per_inst ? ninst : 0);
+    if (per_inst)
+        for (uint32_t i = 0; i < ninst; ++i) inst_supersteps[i] = 1;
     for (;;) {
         const uint32_t nb = (f + kFrBlock - 1) / kFrBlock;
         if (timing) IPG_CUDA(cudaEventRecord(ev[0], st));
@@ -434,6 +489,15 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
         fr_write_kernel<<<nb, kFrThreads, 0, st>>>(g->frontier[cur], f, g->off, val, g->block_sums, g->fr_prefix,
                                                    g->fr_rowstart, g->fr_val);
         IPG_CUDA(cudaGetLastError());
+        if (per_inst) {
+            IPG_CUDA(cudaMemsetAsync(g->inst_msgs, 0, sizeof(unsigned long long) * ninst, st));
+            const size_t shm = ninst <= 2048 ? sizeof(unsigned long long) * ninst : 0;
+            instance_msgs_kernel<<<grid_cap(f), 256, shm, st>>>(g->frontier[cur], f, g->off, g->perm, g->inst_base,
+                                                                ninst, g->inst_msgs);
+            IPG_CUDA(cudaGetLastError());
+            IPG_CUDA(cudaMemcpyAsync(h_inst.data(), g->inst_msgs, sizeof(unsigned long long) * ninst,
+                                     cudaMemcpyDeviceToHost, st));
+        }
         // direction: a superstep whose messages reach m / pull_divisor runs in pull form
         bool pull = false;
         const long long div = tuning().pull_divisor;
@@ -458,6 +522,8 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
         IPG_CUDA(cudaMemcpyAsync(g->h_counters, g->counters, sizeof(PushCounters), cudaMemcpyDeviceToHost, st));
         IPG_CUDA(cudaStreamSynchronize(st));
         const PushCounters h = *g->h_counters;
+        if (per_inst)
+            for (uint32_t i = 0; i < ninst; ++i) inst_supersteps[i] += h_inst[i] > 0 ? 1 : 0;
         if (h.status & kStatusOverflow) {
             if (stats) stats->count = 0;
             return set_error(IPG_EOVERFLOW, "%s: a path length reached UINT32_MAX", name);
@@ -555,6 +621,43 @@ static ipg_status host_variant(ipg_graph* g, int kind, uint32_t source, uint32_t
 
 ipg_status ipg_hashmin_cc(ipg_graph* g, uint32_t* labels_out, ipg_stats* stats) {
     return host_variant(g, kHashmin, 0, labels_out, stats);
+}
+
+ipg_status ipg_hashmin_cc_batch_dev(ipg_graph* g, uint32_t* labels_dev, uint32_t* supersteps_out, void* stream) {
+    if (!g) return set_error(IPG_EINVAL, "ipg_hashmin_cc_batch: graph is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    DeviceGuard guard(g->device);
+    if (!g->instances) {  // a plain graph is one instance
+        ipg_stats stats{nullptr, 0, 0, 0, 0};
+        IPG_TRY(push_run(g, kHashmin, 0, labels_dev, &stats, st));
+        if (supersteps_out) supersteps_out[0] = stats.count;
+        return IPG_OK;
+    }
+    std::vector<uint32_t> counts(g->instances);
+    IPG_TRY(push_run(g, kHashmin, 0, labels_dev, nullptr, st, counts.data()));
+    if (g->n) {
+        local_labels_kernel<<<grid_cap(g->n), 256, 0, st>>>(labels_dev, g->n, g->inst_base, g->instances);
+        IPG_CUDA(cudaGetLastError());
+        IPG_CUDA(cudaStreamSynchronize(st));
+    }
+    if (supersteps_out)
+        for (uint32_t i = 0; i < g->instances; ++i) supersteps_out[i] = counts[i];
+    return IPG_OK;
+}
+
+ipg_status ipg_hashmin_cc_batch(ipg_graph* g, uint32_t* labels_out, uint32_t* supersteps_out) {
+    if (!g) return set_error(IPG_EINVAL, "ipg_hashmin_cc_batch: graph is NULL");
+    if (g->n && !labels_out) return set_error(IPG_EINVAL, "ipg_hashmin_cc_batch: output is NULL");
+    DeviceGuard guard(g->device);
+    size_t cap = g->val_stage ? (size_t)g->n * sizeof(uint32_t) : 0;
+    if (!g->val_stage) IPG_TRY(ensure(&g->val_stage, &cap, (size_t)g->n));
+    IPG_TRY(ipg_hashmin_cc_batch_dev(g, g->val_stage, supersteps_out, g->stream));
+    if (g->n) {
+        IPG_CUDA(cudaMemcpyAsync(labels_out, g->val_stage, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost,
+                                 g->stream));
+        IPG_CUDA(cudaStreamSynchronize(g->stream));
+    }
+    return IPG_OK;
 }
 
 ipg_status ipg_sssp(ipg_graph* g, uint32_t source, uint32_t* dist_out, ipg_stats* stats) {

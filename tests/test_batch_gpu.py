@@ -92,3 +92,71 @@ def test_batch_device_entry_and_errors(ipg):
     assert e.value.status == 7
     dist, steps = ipg.ipg_sssp_batch(h, [])
     assert dist.shape == (0, g.n)
+
+
+# ---------------------------------------------------------------------------------------
+# many graphs in one object: Hashmin on every instance at once
+
+
+@pytest.fixture(params=["auto", "push", "pull"])
+def direction(request, ipg):
+    old = ipg.ipg_get_tuning("pull_divisor")
+    ipg.ipg_set_tuning("pull_divisor", {"auto": old, "push": 0, "pull": 1 << 40}[request.param])
+    yield request.param
+    ipg.ipg_set_tuning("pull_divisor", old)
+
+
+def _instances(seed):
+    rng = np.random.default_rng(seed)
+    out = [gen.csr_from_edges(0, [], [], undirected=True),  # an empty instance
+           gen.csr_from_edges(1, [], [], undirected=True),
+           gen.csr_from_edges(5, [0, 1, 3], [1, 2, 3], undirected=True)]
+    for i in range(6):
+        out.append(gen.random_multigraph(int(rng.integers(1, 400)), int(rng.integers(0, 900)), seed=seed * 10 + i,
+                                         undirected=True))
+    for sc in (6, 9, 12):
+        out.append(gen.rmat(sc, 8, seed=sc + seed, undirected=True))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_hashmin_batch_matches_each_instance(ipg, direction, seed):
+    graphs = _instances(seed)
+    hb = ipg.ipg_graph_create_batch(graphs, directed=False)
+    count, bases = ipg.ipg_graph_instances(hb)
+    assert count == len(graphs) and bases[-1] == sum(g.n for g in graphs)
+    labels, steps = ipg.ipg_hashmin_cc_batch(hb)
+    for i, g in enumerate(graphs):
+        mine = labels[bases[i]:bases[i + 1]]
+        ref = oracle.hashmin(g.n, g.offsets, g.cols)
+        np.testing.assert_array_equal(mine, ref.values)
+        assert steps[i] == ref.supersteps, (i, steps[i], ref.supersteps)
+        if g.n:
+            h = ipg.ipg_graph_create(g.offsets, g.cols, None, g.n, g.m, False)
+            alone, cnt, _ = ipg.ipg_hashmin_cc(h)
+            np.testing.assert_array_equal(mine, alone)
+            assert cnt == steps[i]
+
+
+def test_hashmin_batch_device_and_errors(ipg):
+    import torch
+
+    graphs = _instances(7)
+    hb = ipg.ipg_graph_create_batch(graphs, directed=False)
+    labels, steps = ipg.ipg_hashmin_cc_batch(hb)
+    t = torch.empty(labels.size, dtype=torch.int32, device="cuda")
+    steps2 = ipg.ipg_hashmin_cc_batch_dev(hb, t)
+    np.testing.assert_array_equal(t.cpu().numpy().view(np.uint32), labels)
+    np.testing.assert_array_equal(steps, steps2)
+    bad = gen.csr_from_edges(3, [0], [1])
+    bad.cols = np.array([7], dtype=np.uint32)  # column beyond its own instance
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_graph_create_batch([graphs[3], bad], directed=False)
+    assert e.value.status == 1
+    # a plain graph is one instance
+    g = gen.rmat(8, 8, seed=2, undirected=True)
+    h = ipg.ipg_graph_create(g.offsets, g.cols, None, g.n, g.m, False)
+    lab, st = ipg.ipg_hashmin_cc_batch(h)
+    ref = oracle.hashmin(g.n, g.offsets, g.cols)
+    np.testing.assert_array_equal(lab, ref.values)
+    assert list(st) == [ref.supersteps]
