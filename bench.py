@@ -45,9 +45,12 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["billion", "batch", "cc-batch"], default="billion",
+    p.add_argument("--workload", choices=["billion", "batch", "cc-batch", "serve"], default="billion",
                    help="billion: the default bench line; batch: 256-source batched SSSP vs one at a time; "
-                        "cc-batch: 64 uneven Hashmin graphs in one object vs one at a time")
+                        "cc-batch: 64 uneven Hashmin graphs in one object vs one at a time; "
+                        "serve: Poisson stream of mixed queries on 32 resident graphs")
+    p.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
+    p.add_argument("--requests", type=int, default=10000, help="serve: measured requests (after 10%% warm-up)")
     p.add_argument("--batch-sources", type=int, default=256)
     p.add_argument("--scale", type=int, default=26)
     p.add_argument("--edge-factor", type=int, default=28)
@@ -563,6 +566,106 @@ def run_cc_batch(a, count=64):
         print(json.dumps(line), flush=True)
 
 
+def serve_stream(srv, graphs, requests, rate, seed, warm):
+    """Drive one server with a seeded Poisson stream; returns per-request records of the
+    measured part (latency from the scheduled arrival)."""
+    import paper_2010_01542_gb300 as ipg
+
+    rng = np.random.default_rng(seed)
+    total = requests + warm
+    gaps = rng.exponential(1.0 / rate, size=total)
+    arrivals = np.cumsum(gaps)
+    gsel = rng.integers(0, len(graphs), size=total)
+    kinds = rng.random(size=total)
+    srcs = rng.random(size=total)
+    pools = [[np.empty(g.n, dtype=np.uint32) for _ in range(24)] for g in graphs]
+    free = {i: list(range(24)) for i in range(len(graphs))}
+    owner = {}
+    recs = {}
+
+    def collect(wait_ms):
+        for c in srv.poll(wait_ms):
+            gi, slot, t_arr, kind, batch = owner.pop(c.user)
+            free[gi].append(slot)
+            if c.status != 0:
+                raise RuntimeError(f"query {c.user} failed with status {c.status}")
+            recs[c.user] = (t_arr, c.t_done, kind, c.batch)
+
+    t0 = srv.now() + 0.05
+    for i in range(total):
+        gi = int(gsel[i])
+        kind = ipg.IPG_Q_SSSP if kinds[i] < 0.6 else (ipg.IPG_Q_HASHMIN if kinds[i] < 0.9 else ipg.IPG_Q_PAGERANK)
+        while not free[gi]:
+            collect(1)
+        t_arr = t0 + arrivals[i]
+        while srv.now() < t_arr:
+            collect(0)
+        slot = free[gi].pop()
+        out = pools[gi][slot]
+        if kind == ipg.IPG_Q_PAGERANK:
+            out = out.view(np.float32)
+        owner[i] = (gi, slot, t_arr, kind, 0)
+        srv.submit(gi, kind, out, source=int(srcs[i] * graphs[gi].n), updates=10, user=i)
+        collect(0)
+    srv.drain()
+    collect(0)
+    return {u: r for u, r in recs.items() if u >= warm}
+
+
+def serve_summary(recs):
+    lat = np.array([(d - a) * 1e3 for a, d, _, _ in recs.values()])
+    t_first = min(a for a, _, _, _ in recs.values())
+    t_last = max(d for _, d, _, _ in recs.values())
+    batches = np.array([b for _, _, k, b in recs.values() if k == 0])
+    shared = np.array([b for _, _, k, b in recs.values() if k != 0])
+    return {"queries_per_s": round(len(recs) / (t_last - t_first), 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+            "sssp_batch_mean": round(float(batches.mean()), 2) if batches.size else None,
+            "cc_pr_shared_run_mean": round(float(shared.mean()), 2) if shared.size else None}
+
+
+def run_serve(a, count=32):
+    """Config: 32 undirected weighted R-MAT graphs (EF 16, scale_i = 12 + splitmix64(splitmix64(seed)
+    + i) % 11, graph seeds 101..132) resident on the GPU; a seeded Poisson stream of --rate requests/s:
+    60% SSSP from a uniform random source, 30% Hashmin, 10% PageRank (10 supersteps).  The
+    continuous-batching server (8 workers, SSSP batches up to 256) against one worker without
+    batching, on the same stream."""
+    import gen
+    import paper_2010_01542_gb300 as ipg
+
+    world, rank, local = dist_init(a)
+    ipg.load_library()
+    base = gen.splitmix64(a.seed)
+    scales = [12 + gen.splitmix64((base + i) & 0xFFFFFFFFFFFFFFFF) % 11 for i in range(count)]
+    graphs = [gen.rmat_device(sc, 16, seed=101 + i, undirected=True, weighted=True, device=local).to_host()
+              for i, sc in enumerate(scales)]
+    handles = [ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, False) for g in graphs]
+    warm = max(a.requests // 10, 100)
+    res = {}
+    for name, kw, rate in (("continuous_batching", dict(workers=8, max_batch=256), a.rate),
+                           ("one_at_a_time", dict(workers=1, max_batch=1), a.rate),
+                           ("continuous_batching_at_75pct_rate", dict(workers=8, max_batch=256), 0.75 * a.rate)):
+        srv = ipg.Server(handles, **kw)
+        recs = serve_stream(srv, graphs, a.requests, rate, a.seed, warm)
+        srv.close()
+        res[name] = serve_summary(recs)
+        res[name]["offered_per_s"] = rate
+    if rank == 0:
+        cb = res["continuous_batching"]
+        line = {"metric": "served queries/s with p50/p99 latency (Poisson arrivals, mixed SSSP/CC/PageRank)",
+                "unit": "queries/s", "value": cb["queries_per_s"], "n_gpus": world, "steps": a.requests,
+                "warmup": warm, "ms_per_step": cb["mean_ms"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32+f32", "data": "synthetic",
+                "config": {"workload": f"{count} undirected weighted R-MAT graphs, EF 16, scales 12..22, "
+                                       f"Poisson {a.rate:g} req/s, 60% SSSP / 30% Hashmin / 10% PageRank, "
+                                       f"seed {a.seed}", "scales": scales,
+                           "total_m": int(sum(g.m for g in graphs))},
+                "p50_ms": cb["p50_ms"], "p99_ms": cb["p99_ms"], "continuous_batching": cb,
+                "one_at_a_time": res["one_at_a_time"],
+                "continuous_batching_at_75pct_rate": res["continuous_batching_at_75pct_rate"]}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -571,6 +674,8 @@ def main():
         run_batch(a)
     elif a.workload == "cc-batch":
         run_cc_batch(a)
+    elif a.workload == "serve":
+        run_serve(a)
     else:
         run_ours(a)
 

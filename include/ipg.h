@@ -220,6 +220,70 @@ ipg_status ipg_sssp_noalloc(const uint64_t* offsets_dev, const uint32_t* columns
                             void* stream);
 
 /*
+ * Serving (not in the paper): a resident set of graphs answering a stream of
+ * queries with continuous batching.  Worker threads take the graph whose head
+ * query has waited longest (one worker per graph at a time); all of its queued
+ * SSSP queries run together (ipg_sssp_batch), which lets queries that arrived
+ * while the previous dispatch was on the GPU join the next one; queued Hashmin
+ * queries (or PageRank queries with the same update count) on one graph share
+ * one run, as they compute the same result (in flight only: completed results
+ * are never reused).  Different graphs run concurrently on their own
+ * streams.  Before a dispatch the server checks that the graph's workspace
+ * fits (free device memory minus reserve_bytes, or workspace_budget when
+ * nonzero), releasing idle graphs' workspaces least recently used first.
+ * Each result equals that of the matching single-query call.
+ * The graphs stay owned by the caller and must outlive the server; while the
+ * server exists, the caller must not call other functions on them.
+ */
+typedef struct ipg_server ipg_server;
+
+typedef enum { IPG_Q_SSSP = 0, IPG_Q_HASHMIN = 1, IPG_Q_PAGERANK = 2 } ipg_query_kind;
+
+typedef struct {
+    uint32_t graph;    /* index into the server's graph array */
+    uint32_t kind;     /* ipg_query_kind */
+    uint32_t source;   /* SSSP source (< n) */
+    uint32_t updates;  /* PageRank updates */
+    void* out;         /* host buffer, caller-owned until the completion: n uint32 (SSSP
+                          distances, Hashmin labels) or n float (PageRank) */
+    uint64_t user;     /* caller's tag, returned in the completion */
+} ipg_query;
+
+typedef struct {
+    uint64_t user;
+    ipg_status status;
+    uint32_t supersteps;  /* superstep count of the query's run */
+    uint32_t batch;       /* queries dispatched together with this one (itself included) */
+    uint32_t reserved;
+    double t_submit;      /* seconds on the server clock (ipg_server_now) */
+    double t_start;
+    double t_done;
+} ipg_completion;
+
+typedef struct {
+    uint32_t workers;           /* worker threads = graphs in flight at once; 0 -> 8 */
+    uint32_t max_batch;         /* SSSP queries dispatched together at most; 0 -> 256 */
+    uint64_t workspace_budget;  /* bytes of graph workspace held at once; 0 -> free memory */
+    uint64_t reserve_bytes;     /* device memory kept free when budget is 0; 0 -> 1 GiB */
+} ipg_server_options;
+
+/* graphs: count graph handles (all on the same device); opt may be NULL. */
+ipg_status ipg_server_create(ipg_graph* const* graphs, uint32_t count, const ipg_server_options* opt,
+                             ipg_server** out);
+/* Queue a query (copied); returns at once.  IPG_EINVAL for a bad graph index,
+ * kind, source, or Hashmin on a directed graph. */
+ipg_status ipg_server_submit(ipg_server* s, const ipg_query* q);
+/* Up to cap completed queries into out; waits up to wait_ms for the first one
+ * (0: no wait, < 0: until one completes or nothing is in flight). */
+uint32_t ipg_server_poll(ipg_server* s, ipg_completion* out, uint32_t cap, int wait_ms);
+/* Wait until every submitted query has completed (completions stay pollable). */
+ipg_status ipg_server_drain(ipg_server* s);
+/* Seconds since the server was created (the clock of the completion times). */
+double ipg_server_now(const ipg_server* s);
+/* Drain, stop the workers, free the server (not the graphs). */
+void ipg_server_destroy(ipg_server* s);
+
+/*
  * Process-wide tuning knobs (not in the paper; they change speed, never results):
  *   "pull_divisor"  Hashmin/SSSP superstep direction.  A superstep whose messages
  *                   (sum of the senders' out-degrees) reach m / pull_divisor runs in

@@ -445,3 +445,106 @@ def ipg_hashmin_cc_batch_dev(g: Graph, labels_dev, stream=None):
 
 
 __all__ += ["ipg_graph_create_batch", "ipg_graph_instances", "ipg_hashmin_cc_batch", "ipg_hashmin_cc_batch_dev"]
+
+
+# ---------------------------------------------------------------------------------------
+# serving
+
+IPG_Q_SSSP, IPG_Q_HASHMIN, IPG_Q_PAGERANK = 0, 1, 2
+
+
+class _CQuery(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_uint32), ("kind", ctypes.c_uint32), ("source", ctypes.c_uint32),
+                ("updates", ctypes.c_uint32), ("out", ctypes.c_void_p), ("user", ctypes.c_uint64)]
+
+
+class _CCompletion(ctypes.Structure):
+    _fields_ = [("user", ctypes.c_uint64), ("status", ctypes.c_int), ("supersteps", ctypes.c_uint32),
+                ("batch", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class _COptions(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("workspace_budget", ctypes.c_uint64),
+                ("reserve_bytes", ctypes.c_uint64)]
+
+
+@dataclass
+class Completion:
+    user: int
+    status: int
+    supersteps: int
+    batch: int
+    t_submit: float
+    t_start: float
+    t_done: float
+    out: Optional[np.ndarray] = None
+
+
+class Server:
+    """Binding of ipg_server_*: graphs stay resident, queries are served with continuous
+    batching by the library's worker threads.  Output arrays are kept alive here until their
+    completion is polled."""
+
+    def __init__(self, graphs, workers: int = 0, max_batch: int = 0, workspace_budget: int = 0,
+                 reserve_bytes: int = 0):
+        lib = load_library()
+        self._lib = lib
+        self._graphs = list(graphs)
+        lib.ipg_server_create.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(_COptions),
+                                          ctypes.POINTER(ctypes.c_void_p)]
+        lib.ipg_server_create.restype = ctypes.c_int
+        lib.ipg_server_submit.argtypes = [ctypes.c_void_p, ctypes.POINTER(_CQuery)]
+        lib.ipg_server_submit.restype = ctypes.c_int
+        lib.ipg_server_poll.argtypes = [ctypes.c_void_p, ctypes.POINTER(_CCompletion), ctypes.c_uint32, ctypes.c_int]
+        lib.ipg_server_poll.restype = ctypes.c_uint32
+        lib.ipg_server_drain.argtypes = [ctypes.c_void_p]
+        lib.ipg_server_drain.restype = ctypes.c_int
+        lib.ipg_server_now.argtypes = [ctypes.c_void_p]
+        lib.ipg_server_now.restype = ctypes.c_double
+        lib.ipg_server_destroy.argtypes = [ctypes.c_void_p]
+        lib.ipg_server_destroy.restype = None
+        handles = (ctypes.c_void_p * len(self._graphs))(*[g.handle for g in self._graphs])
+        opt = _COptions(workers, max_batch, workspace_budget, reserve_bytes)
+        h = ctypes.c_void_p()
+        _check(lib.ipg_server_create(handles, len(self._graphs), ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+        self._outs = {}
+        self._buf = (_CCompletion * 1024)()
+
+    def submit(self, graph: int, kind: int, out: np.ndarray, source: int = 0, updates: int = 10, user: int = 0):
+        q = _CQuery(graph, kind, source, updates, out.ctypes.data if out.size else None, user)
+        self._outs[user] = out
+        try:
+            _check(self._lib.ipg_server_submit(self._h, ctypes.byref(q)))
+        except Exception:
+            self._outs.pop(user, None)
+            raise
+
+    def poll(self, wait_ms: int = 0) -> List[Completion]:
+        k = self._lib.ipg_server_poll(self._h, self._buf, len(self._buf), wait_ms)
+        res = []
+        for c in self._buf[:k]:
+            res.append(Completion(int(c.user), int(c.status), int(c.supersteps), int(c.batch), float(c.t_submit),
+                                  float(c.t_start), float(c.t_done), self._outs.pop(int(c.user), None)))
+        return res
+
+    def drain(self):
+        _check(self._lib.ipg_server_drain(self._h))
+
+    def now(self) -> float:
+        return float(self._lib.ipg_server_now(self._h))
+
+    def close(self):
+        if self._h:
+            self._lib.ipg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+__all__ += ["Server", "Completion", "IPG_Q_SSSP", "IPG_Q_HASHMIN", "IPG_Q_PAGERANK"]

@@ -113,17 +113,47 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
             }
             // only in-edges whose source sends for some lane of the group
             unsigned active = __ballot_sync(0xFFFFFFFFu, sm_l != 0);
+            if (!active) continue;
+            const uint32_t jmax = j0 + 31 - __clz(active);  // last active edge of the group
+            if (jmax < bound) {
+                // fast path: every active edge of the group belongs to the current row
+                while (active) {
+                    uint32_t s[kUnroll], lim[kUnroll];
+#pragma unroll
+                    for (int q = 0; q < kUnroll; ++q) {
+                        const int jj = active ? __ffs(active) - 1 : 0;
+                        const bool ok = active != 0;
+                        if (active) active &= active - 1;
+                        const uint32_t u = __shfl_sync(0xFFFFFFFFu, u_l, jj);
+                        const uint32_t w = __shfl_sync(0xFFFFFFFFu, w_l, jj);
+                        lim[q] = kInf - w;  // s + w stays below kInf iff s < lim
+                        s[q] = ok ? __ldg(sval + ((uint64_t)u * kLanes + lane)) : kInf;
+                    }
+#pragma unroll
+                    for (int q = 0; q < kUnroll; ++q) {
+                        if (s[q] < lim[q]) {
+                            run = min(run, s[q] + (kInf - lim[q]));
+                        } else if (s[q] != kInf) {
+                            atomicOr(&ctr->status, kStatusOverflow);
+                            run = min(run, kInf - 1);
+                        }
+                    }
+                }
+                pending = true;
+                continue;
+            }
             while (active) {
                 int jj[kUnroll];
-                uint32_t s[kUnroll], w[kUnroll];
+                uint32_t s[kUnroll], lim[kUnroll];
 #pragma unroll
                 for (int q = 0; q < kUnroll; ++q) {
                     jj[q] = active ? __ffs(active) - 1 : -1;
                     if (active) active &= active - 1;
                     const int src_lane = jj[q] < 0 ? 0 : jj[q];
                     const uint32_t u = __shfl_sync(0xFFFFFFFFu, u_l, src_lane);
-                    w[q] = __shfl_sync(0xFFFFFFFFu, w_l, src_lane);
-                    s[q] = jj[q] >= 0 ? __ldg(sval + (uint64_t)u * kLanes + lane) : kInf;  // one 128-byte line
+                    const uint32_t w = __shfl_sync(0xFFFFFFFFu, w_l, src_lane);
+                    lim[q] = kInf - w;
+                    s[q] = jj[q] >= 0 ? __ldg(sval + ((uint64_t)u * kLanes + lane)) : kInf;  // one 128-byte line
                 }
 #pragma unroll
                 for (int q = 0; q < kUnroll; ++q) {
@@ -138,13 +168,11 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
                                 bound = (uint32_t)(csc_off[row + 1] - e_begin);
                             } while (e >= bound);
                         }
-                        if (s[q] != kInf) {
-                            unsigned long long d = (unsigned long long)s[q] + w[q];
-                            if (d >= kInf) {
-                                atomicOr(&ctr->status, kStatusOverflow);
-                                d = kInf - 1;
-                            }
-                            run = min(run, (uint32_t)d);
+                        if (s[q] < lim[q]) {
+                            run = min(run, s[q] + (kInf - lim[q]));
+                        } else if (s[q] != kInf) {
+                            atomicOr(&ctr->status, kStatusOverflow);
+                            run = min(run, kInf - 1);
                         }
                         pending = true;
                     }

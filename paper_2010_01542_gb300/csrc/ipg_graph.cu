@@ -311,6 +311,15 @@ __global__ void invert_kernel(const uint32_t* __restrict__ perm, uint32_t n, uin
     if (blockIdx.x == 0 && threadIdx.x == 0) new_deg[n] = 0;
 }
 
+__global__ void max_degree_kernel(const uint64_t* __restrict__ off, uint32_t n, unsigned long long* out) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long mx = 0;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        mx = max(mx, (unsigned long long)(off[v + 1] - off[v]));
+    for (int s = 16; s > 0; s >>= 1) mx = max(mx, __shfl_down_sync(0xFFFFFFFFu, mx, s));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
 __global__ void max_weight_kernel(const uint32_t* __restrict__ w, uint64_t m, unsigned int* out) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     unsigned mx = 0;
@@ -412,7 +421,13 @@ static ipg_status relabel(ipg_graph* g, cudaStream_t st) {
                                                                                 new_off, n, new_col, new_w, new_w8);
         RL(cudaGetLastError());
     }
+    RL(cudaMemsetAsync(&g->counters->receivers, 0, sizeof(unsigned long long), st));
+    max_degree_kernel<<<grid_for(n, sms), 256, 0, st>>>(g->off, n, &g->counters->receivers);
+    RL(cudaGetLastError());
+    RL(cudaMemcpyAsync(&g->h_counters->receivers, &g->counters->receivers, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, st));
     RL(cudaStreamSynchronize(st));
+    g->max_outdeg = g->h_counters->receivers;
     cudaFree(g->off);
     cudaFree(g->col);
     if (g->w) cudaFree(g->w);
@@ -459,6 +474,37 @@ Tuning& tuning() {
 
 // ---------------------------------------------------------------------------
 // creation
+
+// frees the per-algorithm workspace, keeping the graph (CSR, CSC, numbering)
+void release_workspace(ipg_graph* g) {
+    DeviceGuard guard(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    auto f = [](auto*& p) {
+        if (p) cudaFree(p);
+        p = nullptr;
+    };
+    f(g->inv_outdeg);
+    f(g->pr_box[0]);
+    f(g->pr_box[1]);
+    f(g->pr_rank);
+    f(g->pr_out_stage);
+    g->pr_out_stage_cap = 0;
+    f(g->stamp);
+    f(g->rstamp);
+    f(g->frontier[0]);
+    f(g->frontier[1]);
+    f(g->fr_prefix);
+    f(g->fr_rowstart);
+    f(g->fr_val);
+    f(g->block_sums);
+    g->block_sums_cap = 0;
+    f(g->push_tile_row);
+    g->push_tile_cap = 0;
+    f(g->val_stage);
+    f(g->val);
+    f(g->sval);
+    batch_free(g);
+}
 
 static void free_graph(ipg_graph* g) {
     if (!g) return;

@@ -86,6 +86,7 @@ struct ipg_graph {
     uint32_t* col = nullptr;
     uint32_t* w = nullptr;       // u32 weights (only when some weight exceeds 255)
     uint8_t* w8 = nullptr;       // u8 weights (when every weight fits in a byte)
+    uint64_t max_outdeg = 0;     // largest out-degree (bounds a frontier's messages)
     uint32_t* perm = nullptr;    // internal id -> caller's id
     uint32_t* inv = nullptr;     // caller's id -> internal id
 

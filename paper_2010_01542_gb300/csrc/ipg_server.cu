@@ -1,0 +1,352 @@
+// Serving loop: a resident set of graphs answering a stream of mixed queries
+// (SSSP, Hashmin CC, PageRank), with continuous batching.
+//
+// Every graph has a FIFO of pending queries.  Worker threads take the oldest
+// waiting graph that no other worker is running (calls on one graph share its
+// workspace and must not overlap) and dispatch:
+//   - all of that graph's queued SSSP queries together, up to max_batch, through
+//     the batched SSSP engine (queries that arrived while the previous dispatch
+//     was on the GPU join the next one: continuous batching); below 8 queries
+//     the dispatch runs them one source at a time, which is faster there;
+//   - otherwise the head query's kind (Hashmin, or PageRank with the same update
+//     count): every such query queued on the graph shares one run, since they
+//     compute the same result (in flight only: finished results are not reused).
+// Graphs run on their own streams, so the work of different graphs overlaps on
+// the device.  Before a dispatch, the worker checks that the graph's workspace
+// fits next to the others (free device memory minus a reserve, or a fixed
+// budget); if not, it releases the workspace of idle graphs, least recently
+// used first, and otherwise waits for running work to finish.  Results go to
+// the caller's host buffers; completions carry timestamps for latency.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <string.h>
+
+#include "ipg_internal.cuh"
+
+struct ipg_server {
+    struct Pending {
+        ipg_query q;
+        double t_submit;
+    };
+    struct Slot {
+        ipg_graph* g = nullptr;
+        std::deque<Pending> pending;
+        bool busy = false;
+        uint64_t last_used = 0;
+        size_t held = 0;  // workspace bytes this graph holds (estimate)
+    };
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ipg_completion> done;
+    std::vector<std::thread> workers;
+    bool stop = false;
+    uint64_t inflight = 0;
+    uint64_t tick = 0;
+    size_t budget = 0;  // 0: use free device memory minus reserve
+    size_t reserve = 0;
+    uint32_t max_batch = 256;
+    std::chrono::steady_clock::time_point t0;
+    int device = 0;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace ipg {
+
+void release_workspace(ipg_graph* g);  // ipg_graph.cu
+
+namespace {
+
+// fewer queued SSSP queries than this run one source at a time (measured break-even of
+// the batched engine against one-source runs is about 8-12 sources on R-MAT 22/16)
+constexpr size_t kMinSsspBatch = 8;
+
+
+// device bytes a dispatch may still need to allocate on this graph
+size_t workspace_need(const ipg_graph* g, uint32_t kind, uint32_t k) {
+    const size_t n = g->n, m = g->m;
+    const size_t tiles = (n + m) / 2048 + 2;
+    size_t need = 0;
+    if (!g->csc_ready && g->directed) need += m * 9 + n * 8;  // in-edges (sources + weights) and offsets
+    if (kind == IPG_Q_PAGERANK) {
+        if (!g->pr_box[0]) need += n * 16 + tiles * 12;
+    } else {
+        if (!g->stamp) need += n * 36 + tiles * 4;
+        if (!g->sval) need += n * 4 + tiles * 12;
+        if (kind == IPG_Q_SSSP && k >= kMinSsspBatch && !g->batch) need += n * 264;
+    }
+    if (!g->val_stage) need += n * 4;
+    return need;
+}
+
+size_t device_free(int device) {
+    size_t fr = 0, tot = 0;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != device) cudaSetDevice(device);
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+    if (prev != device && prev >= 0) cudaSetDevice(prev);
+    return fr;
+}
+
+struct WorkerBuffers {
+    uint32_t* dev = nullptr;  // k * n staging for batched SSSP
+    size_t cap = 0;
+    ~WorkerBuffers() {
+        if (dev) cudaFree(dev);
+    }
+};
+
+void finish(ipg_server* s, const std::vector<ipg_server::Pending>& batch, const std::vector<ipg_status>& rc,
+            const std::vector<uint32_t>& steps, double t_start, double t_done) {
+    for (size_t i = 0; i < batch.size(); ++i) {
+        ipg_completion c{};
+        c.user = batch[i].q.user;
+        c.status = rc[i];
+        c.supersteps = steps[i];
+        c.batch = (uint32_t)batch.size();
+        c.t_submit = batch[i].t_submit;
+        c.t_start = t_start;
+        c.t_done = t_done;
+        s->done.push_back(c);
+    }
+}
+
+void worker_main(ipg_server* s) {
+    cudaSetDevice(s->device);
+    WorkerBuffers buf;
+    std::unique_lock<std::mutex> lock(s->mu);
+    while (!s->stop) {
+        // the idle graph whose head query has waited longest
+        int pick = -1;
+        double oldest = 0;
+        for (size_t i = 0; i < s->slots.size(); ++i) {
+            const auto& sl = s->slots[i];
+            if (sl.busy || sl.pending.empty()) continue;
+            if (pick < 0 || sl.pending.front().t_submit < oldest) {
+                pick = (int)i;
+                oldest = sl.pending.front().t_submit;
+            }
+        }
+        if (pick < 0) {
+            s->cv_work.wait(lock);
+            continue;
+        }
+        auto& slot = s->slots[pick];
+        std::vector<ipg_server::Pending> batch;
+        const uint32_t kind = slot.pending.front().q.kind;
+        if (kind == IPG_Q_SSSP) {
+            for (auto it = slot.pending.begin(); it != slot.pending.end() && batch.size() < s->max_batch;) {
+                if (it->q.kind == IPG_Q_SSSP) {
+                    batch.push_back(*it);
+                    it = slot.pending.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        } else {
+            // Hashmin / PageRank queries queued on this graph compute the same result: they
+            // share one run (in flight only; finished results are never reused)
+            const uint32_t upd = slot.pending.front().q.updates;
+            for (auto it = slot.pending.begin(); it != slot.pending.end() && batch.size() < s->max_batch;) {
+                if (it->q.kind == kind && (kind != IPG_Q_PAGERANK || it->q.updates == upd)) {
+                    batch.push_back(*it);
+                    it = slot.pending.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+        }
+        // admission by device memory
+        const size_t need = workspace_need(slot.g, kind, (uint32_t)batch.size());
+        for (;;) {
+            size_t avail;
+            if (s->budget) {
+                size_t used = 0;
+                for (auto& o : s->slots) used += o.held;
+                avail = s->budget > used ? s->budget - used : 0;
+            } else {
+                const size_t fr = device_free(s->device);
+                avail = fr > s->reserve ? fr - s->reserve : 0;
+            }
+            if (need <= avail) break;
+            // release the least recently used idle workspace
+            int lru = -1;
+            for (size_t i = 0; i < s->slots.size(); ++i) {
+                auto& o = s->slots[i];
+                if ((int)i == pick || o.busy || o.held == 0) continue;
+                if (lru < 0 || o.last_used < s->slots[lru].last_used) lru = (int)i;
+            }
+            if (lru >= 0) {
+                release_workspace(s->slots[lru].g);
+                s->slots[lru].held = 0;
+                continue;
+            }
+            bool others_running = false;
+            for (auto& o : s->slots) others_running |= o.busy;
+            if (!others_running) break;  // nothing to wait for: try, and report ENOMEM if it fails
+            s->cv_done.wait(lock);
+        }
+        slot.busy = true;
+        slot.last_used = ++s->tick;
+        slot.held += need;
+        ipg_graph* g = slot.g;
+        const bool batched = kind == IPG_Q_SSSP && batch.size() >= kMinSsspBatch;
+        lock.unlock();
+
+        const double t_start = s->now();
+        std::vector<ipg_status> rc(batch.size(), IPG_OK);
+        std::vector<uint32_t> steps(batch.size(), 0);
+        if (kind == IPG_Q_SSSP && !batched) {
+            // a few sources: one-source runs (push for sparse supersteps) beat a batch,
+            // which streams every in-edge once per superstep
+            for (size_t i = 0; i < batch.size(); ++i) {
+                ipg_stats st{nullptr, 0, 0, 0, 0};
+                rc[i] = ipg_sssp(g, batch[i].q.source, (uint32_t*)batch[i].q.out, &st);
+                steps[i] = st.count;
+            }
+        } else if (kind == IPG_Q_SSSP) {
+            const size_t k = batch.size(), n = g->n;
+            ipg_status r = IPG_OK;
+            if (buf.cap < k * n) {
+                if (buf.dev) cudaFree(buf.dev);
+                buf.dev = nullptr;
+                buf.cap = 0;
+                if (cudaMalloc(&buf.dev, sizeof(uint32_t) * (k * n ? k * n : 1)) != cudaSuccess)
+                    r = set_error(IPG_ENOMEM, "server: staging allocation failed");
+                else
+                    buf.cap = k * n;
+            }
+            std::vector<uint32_t> src(k);
+            for (size_t i = 0; i < k; ++i) src[i] = batch[i].q.source;
+            if (r == IPG_OK) r = sssp_batch_run(g, src.data(), (uint32_t)k, buf.dev, steps.data(), g->stream);
+            for (size_t i = 0; i < k && r == IPG_OK; ++i) {
+                cudaError_t e = cudaMemcpyAsync(batch[i].q.out, buf.dev + i * n, sizeof(uint32_t) * n,
+                                                cudaMemcpyDeviceToHost, g->stream);
+                if (e != cudaSuccess) r = cuda_fail(e, "server result copy", __FILE__, __LINE__);
+            }
+            if (r == IPG_OK) {
+                cudaError_t e = cudaStreamSynchronize(g->stream);
+                if (e != cudaSuccess) r = cuda_fail(e, "server result copy", __FILE__, __LINE__);
+            }
+            std::fill(rc.begin(), rc.end(), r);
+        } else if (kind == IPG_Q_HASHMIN || kind == IPG_Q_PAGERANK) {
+            ipg_stats st{nullptr, 0, 0, 0, 0};
+            const ipg_status r = kind == IPG_Q_HASHMIN
+                                     ? ipg_hashmin_cc(g, (uint32_t*)batch[0].q.out, &st)
+                                     : ipg_pagerank(g, batch[0].q.updates, (float*)batch[0].q.out, &st);
+            for (size_t i = 1; i < batch.size() && r == IPG_OK; ++i)
+                memcpy(batch[i].q.out, batch[0].q.out, sizeof(uint32_t) * (size_t)g->n);
+            std::fill(rc.begin(), rc.end(), r);
+            std::fill(steps.begin(), steps.end(), st.count);
+        } else {
+            rc[0] = set_error(IPG_EINVAL, "server: unknown query kind %u", kind);
+        }
+        const double t_done = s->now();
+
+        lock.lock();
+        slot.busy = false;
+        finish(s, batch, rc, steps, t_start, t_done);
+        s->inflight -= batch.size();
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+}  // namespace ipg
+
+using namespace ipg;
+
+extern "C" {
+
+ipg_status ipg_server_create(ipg_graph* const* graphs, uint32_t count, const ipg_server_options* opt,
+                             ipg_server** out) {
+    if (!out) return set_error(IPG_EINVAL, "ipg_server_create: out is NULL");
+    *out = nullptr;
+    if (!graphs || count == 0) return set_error(IPG_EINVAL, "ipg_server_create: no graphs");
+    for (uint32_t i = 0; i < count; ++i)
+        if (!graphs[i]) return set_error(IPG_EINVAL, "ipg_server_create: graph %u is NULL", i);
+    ipg_server* s = new (std::nothrow) ipg_server();
+    if (!s) return set_error(IPG_ENOMEM, "ipg_server_create: host allocation failed");
+    s->t0 = std::chrono::steady_clock::now();
+    s->device = graphs[0]->device;
+    s->slots.resize(count);
+    for (uint32_t i = 0; i < count; ++i) s->slots[i].g = graphs[i];
+    uint32_t workers = opt && opt->workers ? opt->workers : 8;
+    if (workers > 64) workers = 64;
+    s->max_batch = opt && opt->max_batch ? opt->max_batch : 256;
+    s->budget = opt ? (size_t)opt->workspace_budget : 0;
+    s->reserve = opt && opt->reserve_bytes ? (size_t)opt->reserve_bytes : ((size_t)1 << 30);
+    for (uint32_t w = 0; w < workers; ++w) s->workers.emplace_back(worker_main, s);
+    *out = s;
+    return IPG_OK;
+}
+
+ipg_status ipg_server_submit(ipg_server* s, const ipg_query* q) {
+    if (!s || !q) return set_error(IPG_EINVAL, "ipg_server_submit: NULL argument");
+    if (q->graph >= s->slots.size()) return set_error(IPG_EINVAL, "ipg_server_submit: graph %u out of range", q->graph);
+    const ipg_graph* g = s->slots[q->graph].g;
+    if (q->kind > IPG_Q_PAGERANK) return set_error(IPG_EINVAL, "ipg_server_submit: unknown kind %u", q->kind);
+    if (q->kind == IPG_Q_SSSP && q->source >= g->n)
+        return set_error(IPG_EINVAL, "ipg_server_submit: source %u >= n = %u", q->source, g->n);
+    if (q->kind == IPG_Q_HASHMIN && g->directed)
+        return set_error(IPG_EINVAL, "ipg_server_submit: Hashmin needs an undirected graph");
+    if (g->n && !q->out) return set_error(IPG_EINVAL, "ipg_server_submit: output is NULL");
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->slots[q->graph].pending.push_back({*q, s->now()});
+        s->inflight++;
+    }
+    s->cv_work.notify_one();
+    return IPG_OK;
+}
+
+uint32_t ipg_server_poll(ipg_server* s, ipg_completion* out, uint32_t cap, int wait_ms) {
+    if (!s || !out || cap == 0) return 0;
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (s->done.empty() && wait_ms != 0) {
+        if (wait_ms < 0)
+            s->cv_done.wait(lock, [&] { return !s->done.empty() || s->inflight == 0; });
+        else
+            s->cv_done.wait_for(lock, std::chrono::milliseconds(wait_ms), [&] { return !s->done.empty(); });
+    }
+    uint32_t k = 0;
+    while (k < cap && !s->done.empty()) {
+        out[k++] = s->done.front();
+        s->done.pop_front();
+    }
+    return k;
+}
+
+ipg_status ipg_server_drain(ipg_server* s) {
+    if (!s) return set_error(IPG_EINVAL, "ipg_server_drain: server is NULL");
+    std::unique_lock<std::mutex> lock(s->mu);
+    s->cv_done.wait(lock, [&] { return s->inflight == 0; });
+    return IPG_OK;
+}
+
+double ipg_server_now(const ipg_server* s) { return s ? s->now() : 0.0; }
+
+void ipg_server_destroy(ipg_server* s) {
+    if (!s) return;
+    {
+        std::unique_lock<std::mutex> lock(s->mu);
+        s->cv_done.wait(lock, [&] { return s->inflight == 0; });
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->workers) t.join();
+    delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+"""Serving loop (ipg_server_*): a mixed stream of SSSP, Hashmin and PageRank queries on a
+resident set of graphs.  Every result is the same in the mix as alone (bit for bit: the
+min combiners are exact and PageRank sums in a fixed order), SSSP queries that queue up
+on one graph run batched, and a tight workspace budget forces least-recently-used
+workspace releases without changing any result."""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ipg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2010_01542_gb300 as ipg
+    from paper_2010_01542_gb300 import _build
+
+    _build.build()
+    ipg.load_library()
+    return ipg
+
+
+def _graph_set():
+    out = []
+    for i, sc in enumerate((8, 10, 12, 13, 9, 14)):
+        out.append(gen.rmat(sc, 16, seed=100 + i, undirected=True, weighted=True))
+    return out
+
+
+def _alone(ipg, h, kind, source):
+    if kind == ipg.IPG_Q_SSSP:
+        return ipg.ipg_sssp(h, source)
+    if kind == ipg.IPG_Q_HASHMIN:
+        return ipg.ipg_hashmin_cc(h)
+    return ipg.ipg_pagerank(h, 10)
+
+
+def _mixed_queries(graphs, count, seed):
+    rng = np.random.default_rng(seed)
+    qs = []
+    for u in range(count):
+        gi = int(rng.integers(0, len(graphs)))
+        r = rng.random()
+        kind = 0 if r < 0.6 else (1 if r < 0.9 else 2)
+        qs.append((u, gi, kind, int(rng.integers(0, graphs[gi].n))))
+    return qs
+
+
+@pytest.mark.parametrize("budget", [0, 1 << 22])
+def test_results_same_alone_and_in_the_mix(ipg, budget):
+    graphs = _graph_set()
+    handles = [ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, False) for g in graphs]
+    queries = _mixed_queries(graphs, 300, seed=budget % 7 + 1)
+    # results alone, before the server exists
+    ref = {}
+    for u, gi, kind, src in queries:
+        vals, cnt, _ = _alone(ipg, handles[gi], kind, src)
+        ref[u] = (vals.copy(), cnt)
+    srv = ipg.Server(handles, workers=4, max_batch=64, workspace_budget=budget)
+    done = []
+    for u, gi, kind, src in queries:
+        out = np.empty(graphs[gi].n, dtype=np.float32 if kind == 2 else np.uint32)
+        srv.submit(gi, kind, out, source=src, updates=10, user=u)
+        done += srv.poll(0)
+    srv.drain()
+    done += srv.poll(0)
+    srv.close()
+    assert len(done) == len(queries)
+    batched = 0
+    for c in done:
+        assert c.status == 0
+        vals, cnt = ref[c.user]
+        np.testing.assert_array_equal(c.out.view(np.uint32), vals.view(np.uint32))
+        assert c.supersteps == cnt
+        assert c.t_submit <= c.t_start <= c.t_done
+        batched += c.batch > 1
+    assert batched > 0  # SSSP queries that queued on one graph ran together
+
+
+def test_server_rejects_bad_queries(ipg):
+    g = gen.rmat(8, 8, seed=1, weighted=True)
+    hd = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, True)
+    srv = ipg.Server([hd], workers=1)
+    out = np.empty(g.n, dtype=np.uint32)
+    with pytest.raises(ipg.IpgError):
+        srv.submit(1, ipg.IPG_Q_SSSP, out, source=0)
+    with pytest.raises(ipg.IpgError):
+        srv.submit(0, ipg.IPG_Q_SSSP, out, source=g.n)
+    with pytest.raises(ipg.IpgError):
+        srv.submit(0, ipg.IPG_Q_HASHMIN, out)  # directed graph
+    srv.submit(0, ipg.IPG_Q_SSSP, out, source=0, user=5)
+    srv.drain()
+    (c,) = srv.poll(0)
+    ref, cnt, _ = ipg.ipg_sssp(hd, 0)
+    assert c.user == 5 and c.status == 0 and c.supersteps == cnt
+    np.testing.assert_array_equal(c.out, ref)
+    srv.close()
