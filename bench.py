@@ -94,18 +94,28 @@ def barrier(world):
         import torch.distributed as dist
 
         dist.barrier()
-        torch.cuda.synchronize()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
 
 
 def all_max(x, world):
+    """Max of x over the ranks (the slowest rank's time); works on nccl (CUDA tensor) and gloo."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(units_per_rank, ms_local, world):
+    """Whole-job rate for replicas (weak scaling, no data-path collective): every rank
+    processes units_per_rank; the job takes as long as its slowest rank."""
+    ms = all_max(ms_local, world)
+    return world * units_per_rank / (ms / 1e3), ms
 
 
 # ---------------------------------------------------------------------------------------
@@ -287,12 +297,12 @@ def run_ours(a):
     barrier(world)
     clocks = sampler.stop()
     ms = t_start.elapsed_time(t_end)
-    ms_max = all_max(ms, world)
 
     pr_edges = PR_UPDATES * m
     sssp_edges = [sum(s.messages_sent for s in sst) for _, sst in all_stats]
     edges_per_step = pr_edges + statistics.mean(sssp_edges)
-    value = world * edges_per_step * a.steps / (ms_max / 1e3) / 1e9
+    rate, ms_max = replica_throughput(edges_per_step * a.steps, ms, world)
+    value = rate / 1e9
     pr_kernel_ms = [s.kernel_ms for pst, _ in all_stats for s in pst[:PR_UPDATES]]
     pr_step_ms = [s.superstep_ms for pst, _ in all_stats for s in pst[:PR_UPDATES]]
     sssp_kernel_ms = [sum(s.kernel_ms for s in sst) for _, sst in all_stats]
