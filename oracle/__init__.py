@@ -1,9 +1,11 @@
 """ORACLE — test infrastructure only.
 
 Python access to the plain single-threaded CPU Pregel implementation in
-``oracle/ipg_oracle.c`` (PageRank in float64, Hashmin connected components, SSSP),
-written from the paper's description of the vertex-centric model (Sec. I) and of
-the mailbox with its "has a message" flag (Sec. III).
+``oracle/ipg_oracle.c`` (PageRank in float64, Hashmin connected components, SSSP,
+the shortest-path tree and shortest-path counting with wider messages, and the
+mailbox combination step alone), written from the paper's description of the
+vertex-centric model (Sec. I) and of the mailbox with its "has a message" flag
+and user-defined combine function (Sec. III, Fig. 1).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
 reference legs may import this package.  The library under
@@ -76,6 +78,12 @@ def _lib():
         lib.orc_sssp.restype = i32
         lib.orc_pagerank.argtypes = [u32, vp, vp, u32, vp, vp, u32, ctypes.POINTER(u32)]
         lib.orc_pagerank.restype = i32
+        lib.orc_combine.argtypes = [i32, u32, ctypes.c_uint64, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+        lib.orc_combine.restype = i32
+        lib.orc_sssp_tree.argtypes = [u32, vp, vp, vp, u32, vp, vp, vp, u32, u32, ctypes.POINTER(u32)]
+        lib.orc_sssp_tree.restype = i32
+        lib.orc_bfs_paths.argtypes = [u32, vp, vp, u32, vp, vp, vp, u32, u32, ctypes.POINTER(u32)]
+        lib.orc_bfs_paths.restype = i32
         _lib_handle = lib
     return _lib_handle
 
@@ -134,3 +142,79 @@ def pagerank(n: int, offsets, cols, updates: int = 10) -> Result:
     if rc:
         raise OracleError(f"orc_pagerank failed with code {rc}")
     return Result(rank[:n], int(ss.value), _stats(st, min(ss.value, _CAP)))
+
+
+# combine kinds of orc_combine (same numbering as the C ABI's ipg_combine_kind)
+COMBINE_XOR_U32 = 0
+COMBINE_MIN_U64 = 1
+COMBINE_SUM_U64 = 2
+COMBINE_MINCOUNT_U128 = 3
+_KIND_DTYPE = {COMBINE_XOR_U32: (np.uint32, 1), COMBINE_MIN_U64: (np.uint64, 1), COMBINE_SUM_U64: (np.uint64, 1),
+               COMBINE_MINCOUNT_U128: (np.uint64, 2)}
+
+
+@dataclass
+class CombineResult:
+    has: np.ndarray       # bool[n]: the vertex received at least one message
+    mail: np.ndarray      # combined message per vertex (meaningful where has is True)
+    receivers: int
+
+
+def combine(kind: int, n: int, dst, msgs) -> CombineResult:
+    """Deliver messages msgs[i] to dst[i] into n empty mailboxes (Sec. III).  msgs is a
+    u32[k] (XOR_U32), u64[k] (MIN_U64, SUM_U64) or u64[k, 2] = (key, count) (MINCOUNT_U128)."""
+    dt, width = _KIND_DTYPE[kind]
+    dst = np.ascontiguousarray(dst, dtype=np.uint32)
+    msgs = np.ascontiguousarray(msgs, dtype=dt)
+    k = dst.shape[0]
+    if msgs.shape != ((k,) if width == 1 else (k, 2)):
+        raise ValueError("message array has the wrong shape for this kind")
+    has = np.zeros(max(n, 1), dtype=np.uint8)
+    mail = np.zeros((max(n, 1),) if width == 1 else (max(n, 1), 2), dtype=dt)
+    r = ctypes.c_uint64()
+    rc = _lib().orc_combine(kind, n, k, _ptr(dst), _ptr(msgs), has.ctypes.data, mail.ctypes.data, ctypes.byref(r))
+    if rc:
+        raise OracleError(f"orc_combine failed with code {rc}")
+    return CombineResult(has[:n].astype(bool), mail[:n], int(r.value))
+
+
+@dataclass
+class TreeResult:
+    dist: np.ndarray
+    parent: np.ndarray
+    supersteps: int
+    stats: List[SuperstepStats]
+
+
+def sssp_tree(n: int, offsets, cols, weights, source: int, max_supersteps: int = 0) -> TreeResult:
+    offsets, cols, w = _prep(n, offsets, cols, weights)
+    dist = np.empty(max(n, 1), dtype=np.uint32)
+    parent = np.empty(max(n, 1), dtype=np.uint32)
+    st = (_Stats * _CAP)()
+    ss = ctypes.c_uint32()
+    rc = _lib().orc_sssp_tree(n, _ptr(offsets), _ptr(cols), _ptr(w), source, dist.ctypes.data, parent.ctypes.data,
+                              st, _CAP, max_supersteps, ctypes.byref(ss))
+    if rc:
+        raise OracleError(f"orc_sssp_tree failed with code {rc}")
+    return TreeResult(dist[:n], parent[:n], int(ss.value), _stats(st, min(ss.value, _CAP)))
+
+
+@dataclass
+class PathsResult:
+    level: np.ndarray
+    paths: np.ndarray
+    supersteps: int
+    stats: List[SuperstepStats]
+
+
+def bfs_paths(n: int, offsets, cols, source: int, max_supersteps: int = 0) -> PathsResult:
+    offsets, cols, _ = _prep(n, offsets, cols)
+    level = np.empty(max(n, 1), dtype=np.uint32)
+    paths = np.empty(max(n, 1), dtype=np.uint64)
+    st = (_Stats * _CAP)()
+    ss = ctypes.c_uint32()
+    rc = _lib().orc_bfs_paths(n, _ptr(offsets), _ptr(cols), source, level.ctypes.data, paths.ctypes.data, st, _CAP,
+                              max_supersteps, ctypes.byref(ss))
+    if rc:
+        raise OracleError(f"orc_bfs_paths failed with code {rc}")
+    return PathsResult(level[:n], paths[:n], int(ss.value), _stats(st, min(ss.value, _CAP)))

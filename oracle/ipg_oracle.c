@@ -35,7 +35,12 @@
  * Parity pins: closed forms (PageRank on cycles and stars), library routines
  * (connected components, Dijkstra, BFS from scipy), the PageRank fixed point
  * (a dense linear solve), the superstep-count and per-superstep count closed
- * forms, and the rank-mass identity; see tests/test_oracle_pins.py.
+ * forms, and the rank-mass identity; see tests/test_oracle_pins.py.  The
+ * general-combiner functions (orc_combine, orc_sssp_tree, orc_bfs_paths) are
+ * pinned by numpy ufunc reductions, the parent rule written out from Dijkstra
+ * distances, the shortest-path-count recurrence, grid and hypercube closed
+ * forms, networkx path enumeration and the modulo-2^64 wrap of a diamond
+ * chain; see tests/test_oracle_pins_combiner.py.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -310,5 +315,319 @@ int orc_pagerank(uint32_t n, const uint64_t* off, const uint32_t* col, uint32_t 
     free(msg_next);
     free(has);
     free(has_next);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* mailboxes with an arbitrary combine function and messages of up to 16    */
+/* bytes (Sec. III, the hybrid combiner of Fig. 1).  Sequentially there is   */
+/* no race, so the lock and the compare-and-swap reduce to their meaning:    */
+/* the first message is stored and the flag raised, every later message is   */
+/* combined into the stored one.                                             */
+
+typedef struct {
+    uint64_t a, b; /* the message's fields; which are used depends on the kind */
+} orc_msg;
+
+typedef orc_msg (*orc_combine_fn)(orc_msg x, orc_msg y);
+
+/* kinds of orc_combine */
+#define ORC_COMBINE_XOR_U32 0      /* 4-byte messages, bitwise exclusive or */
+#define ORC_COMBINE_MIN_U64 1      /* 8-byte messages, minimum */
+#define ORC_COMBINE_SUM_U64 2      /* 8-byte messages, sum modulo 2^64 */
+#define ORC_COMBINE_MINCOUNT_U128 3 /* 16-byte (key, count): smallest key, counts of equal keys added */
+
+static orc_msg comb_xor32(orc_msg x, orc_msg y) {
+    orc_msg r = {(uint32_t)(x.a ^ y.a), 0};
+    return r;
+}
+static orc_msg comb_min64(orc_msg x, orc_msg y) { return x.a <= y.a ? x : y; }
+static orc_msg comb_sum64(orc_msg x, orc_msg y) {
+    orc_msg r = {x.a + y.a, 0};
+    return r;
+}
+static orc_msg comb_mincount(orc_msg x, orc_msg y) {
+    if (x.a < y.a) return x;
+    if (y.a < x.a) return y;
+    orc_msg r = {x.a, x.b + y.b};
+    return r;
+}
+
+typedef struct {
+    orc_msg* msg_next;
+    uint8_t* has_next;
+    orc_combine_fn combine;
+    uint64_t sent;
+} gen_mailboxes;
+
+static void send_gen(gen_mailboxes* mb, uint32_t dst, orc_msg m) {
+    mb->sent++;
+    if (mb->has_next[dst]) {
+        mb->msg_next[dst] = mb->combine(mb->msg_next[dst], m);
+    } else {
+        mb->msg_next[dst] = m;
+        mb->has_next[dst] = 1;
+    }
+}
+
+static size_t kind_size(int kind) {
+    switch (kind) {
+        case ORC_COMBINE_XOR_U32: return 4;
+        case ORC_COMBINE_MIN_U64: return 8;
+        case ORC_COMBINE_SUM_U64: return 8;
+        case ORC_COMBINE_MINCOUNT_U128: return 16;
+        default: return 0;
+    }
+}
+
+/*
+ * Deliver k messages, message i to vertex dst[i], into n empty mailboxes, in
+ * the order given.  msgs holds k records of the kind's size (4, 8 or 16 bytes,
+ * little-endian; a 16-byte record is (key u64, count u64)).  On return has[v]
+ * is 1 if vertex v received at least one message, and mail[v] (a record of
+ * the kind's size) holds the combined message; mail[v] is left untouched where
+ * has[v] is 0.  *receivers_out = number of vertices with has[v] = 1.
+ */
+int orc_combine(int kind, uint32_t n, uint64_t k, const uint32_t* dst, const void* msgs, uint8_t* has, void* mail,
+                uint64_t* receivers_out) {
+    size_t sz = kind_size(kind);
+    if (!sz) return ORC_EINVAL;
+    if (k && (!dst || !msgs)) return ORC_EINVAL;
+    if (n && (!has || !mail)) return ORC_EINVAL;
+    for (uint64_t i = 0; i < k; ++i)
+        if (dst[i] >= n) return ORC_EINVAL;
+    gen_mailboxes mb;
+    mb.msg_next = (orc_msg*)calloc(n ? n : 1, sizeof(orc_msg));
+    mb.has_next = has;
+    mb.sent = 0;
+    if (!mb.msg_next) return ORC_ENOMEM;
+    switch (kind) {
+        case ORC_COMBINE_XOR_U32: mb.combine = comb_xor32; break;
+        case ORC_COMBINE_MIN_U64: mb.combine = comb_min64; break;
+        case ORC_COMBINE_SUM_U64: mb.combine = comb_sum64; break;
+        default: mb.combine = comb_mincount; break;
+    }
+    memset(has, 0, n);
+    const unsigned char* in = (const unsigned char*)msgs;
+    for (uint64_t i = 0; i < k; ++i) {
+        orc_msg m = {0, 0};
+        if (sz == 4) {
+            uint32_t x;
+            memcpy(&x, in + i * 4, 4);
+            m.a = x;
+        } else if (sz == 8) {
+            memcpy(&m.a, in + i * 8, 8);
+        } else {
+            memcpy(&m.a, in + i * 16, 8);
+            memcpy(&m.b, in + i * 16 + 8, 8);
+        }
+        send_gen(&mb, dst[i], m);
+    }
+    uint64_t r = 0;
+    unsigned char* out = (unsigned char*)mail;
+    for (uint32_t v = 0; v < n; ++v) {
+        if (!has[v]) continue;
+        r++;
+        if (sz == 4) {
+            uint32_t x = (uint32_t)mb.msg_next[v].a;
+            memcpy(out + (size_t)v * 4, &x, 4);
+        } else if (sz == 8) {
+            memcpy(out + (size_t)v * 8, &mb.msg_next[v].a, 8);
+        } else {
+            memcpy(out + (size_t)v * 16, &mb.msg_next[v].a, 8);
+            memcpy(out + (size_t)v * 16 + 8, &mb.msg_next[v].b, 8);
+        }
+    }
+    if (receivers_out) *receivers_out = r;
+    free(mb.msg_next);
+    return ORC_OK;
+}
+
+/* lexicographic order on (distance, parent) pairs held in a message's a and b */
+static orc_msg comb_lexmin(orc_msg x, orc_msg y) {
+    if (x.a != y.a) return x.a < y.a ? x : y;
+    return x.b <= y.b ? x : y;
+}
+
+/*
+ * Shortest-path tree: SSSP (Sec. VI-C) whose message carries the sender's id
+ * as well as the distance, combined by the lexicographic minimum of
+ * (distance, sender).
+ * State of v: (dist, parent), initially (infinity, infinity).
+ * compute(v), superstep 0: the source takes (0, source) and sends.
+ * compute(v), superstep s > 0: (d, p) = combined message; if (d, p) is
+ *   lexicographically below (dist, parent) the state becomes (d, p); if the
+ *   distance itself dropped, send (dist + w(v,u), v) to every out-neighbour u.
+ *   Vote to halt.
+ * The senders are exactly those of orc_sssp, so the superstep count and every
+ * per-superstep count equal SSSP's.  The final parent of a reached vertex v
+ * other than the source is the smallest u with an edge u -> v and
+ * dist[u] + w(u,v) = dist[v]; the source's parent is itself; an unreached
+ * vertex keeps (infinity, infinity).
+ */
+int orc_sssp_tree(uint32_t n, const uint64_t* off, const uint32_t* col, const uint32_t* w, uint32_t source,
+                  uint32_t* dist, uint32_t* parent, orc_stats* st, uint32_t cap, uint32_t max_supersteps,
+                  uint32_t* supersteps_out) {
+    int rc = check_csr(n, off, col);
+    if (rc) return rc;
+    if (source >= n || !dist || !parent) return ORC_EINVAL;
+    size_t k = n ? n : 1;
+    gen_mailboxes mb;
+    orc_msg* msg = (orc_msg*)calloc(k, sizeof(orc_msg));
+    uint8_t* has = (uint8_t*)calloc(k, 1);
+    mb.msg_next = (orc_msg*)calloc(k, sizeof(orc_msg));
+    mb.has_next = (uint8_t*)calloc(k, 1);
+    mb.combine = comb_lexmin;
+    if (!msg || !has || !mb.msg_next || !mb.has_next) {
+        free(msg);
+        free(has);
+        free(mb.msg_next);
+        free(mb.has_next);
+        return ORC_ENOMEM;
+    }
+    for (uint32_t v = 0; v < n; ++v) {
+        dist[v] = ORC_INF;
+        parent[v] = ORC_INF;
+    }
+    uint32_t s = 0;
+    uint64_t active = n;
+    rc = ORC_OK;
+    for (;;) {
+        uint64_t senders = 0;
+        mb.sent = 0;
+        for (uint32_t v = 0; v < n; ++v) {
+            int runs = (s == 0) || has[v];
+            if (!runs) continue;
+            orc_msg cand;
+            if (s == 0) {
+                cand.a = v == source ? 0u : ORC_INF;
+                cand.b = v == source ? source : ORC_INF;
+            } else {
+                cand = msg[v];
+            }
+            int lower = cand.a < dist[v] || (cand.a == dist[v] && cand.b < parent[v]);
+            if (!lower) continue;
+            int dist_dropped = cand.a < dist[v];
+            dist[v] = (uint32_t)cand.a;
+            parent[v] = (uint32_t)cand.b;
+            if (!dist_dropped) continue;
+            senders++;
+            for (uint64_t e = off[v]; e < off[v + 1]; ++e) {
+                uint64_t len = w ? (uint64_t)w[e] : 1u;
+                uint64_t d = (uint64_t)dist[v] + len;
+                if (d >= ORC_INF) {
+                    rc = ORC_EOVERFLOW;
+                    d = ORC_INF - 1;
+                }
+                orc_msg m = {d, v};
+                send_gen(&mb, col[e], m);
+            }
+        }
+        uint64_t sent = mb.sent;
+        /* deliver */
+        orc_msg* tm = msg;
+        msg = mb.msg_next;
+        mb.msg_next = tm;
+        uint8_t* th = has;
+        has = mb.has_next;
+        mb.has_next = th;
+        memset(mb.has_next, 0, k);
+        uint64_t receivers = 0;
+        for (uint32_t v = 0; v < n; ++v) receivers += has[v];
+        record(st, cap, s, active, senders, sent, receivers);
+        s++;
+        if (sent == 0) break;
+        if (max_supersteps && s >= max_supersteps) break;
+        active = receivers;
+    }
+    if (supersteps_out) *supersteps_out = s;
+    free(msg);
+    free(has);
+    free(mb.msg_next);
+    free(mb.has_next);
+    return rc;
+}
+
+/*
+ * Shortest-path counting by breadth-first levels: each message carries
+ * (level, number of paths) and the combine keeps the smallest level and adds
+ * the counts of messages at that level (ORC_COMBINE_MINCOUNT_U128).  Edges
+ * have length 1 whatever the graph's weights; every edge is one message, so
+ * parallel edges count as distinct paths.  Counts are taken modulo 2^64.
+ * State of v: (level, paths), initially (infinity, 0).
+ * compute(v), superstep 0: the source takes (0, 1) and sends.
+ * compute(v), superstep s > 0: if v has no level yet, it takes the combined
+ *   message as its state and sends (level + 1, paths) to every out-neighbour.
+ *   Vote to halt.
+ * Result: level = hop distance from the source (infinity if unreached), paths
+ * = number of shortest paths from the source modulo 2^64 (0 if unreached).
+ */
+int orc_bfs_paths(uint32_t n, const uint64_t* off, const uint32_t* col, uint32_t source, uint32_t* level,
+                  uint64_t* paths, orc_stats* st, uint32_t cap, uint32_t max_supersteps, uint32_t* supersteps_out) {
+    int rc = check_csr(n, off, col);
+    if (rc) return rc;
+    if (source >= n || !level || !paths) return ORC_EINVAL;
+    size_t k = n ? n : 1;
+    gen_mailboxes mb;
+    orc_msg* msg = (orc_msg*)calloc(k, sizeof(orc_msg));
+    uint8_t* has = (uint8_t*)calloc(k, 1);
+    mb.msg_next = (orc_msg*)calloc(k, sizeof(orc_msg));
+    mb.has_next = (uint8_t*)calloc(k, 1);
+    mb.combine = comb_mincount;
+    if (!msg || !has || !mb.msg_next || !mb.has_next) {
+        free(msg);
+        free(has);
+        free(mb.msg_next);
+        free(mb.has_next);
+        return ORC_ENOMEM;
+    }
+    for (uint32_t v = 0; v < n; ++v) {
+        level[v] = ORC_INF;
+        paths[v] = 0;
+    }
+    uint32_t s = 0;
+    uint64_t active = n;
+    for (;;) {
+        uint64_t senders = 0;
+        mb.sent = 0;
+        for (uint32_t v = 0; v < n; ++v) {
+            int runs = (s == 0) || has[v];
+            if (!runs) continue;
+            if (s == 0) {
+                if (v != source) continue;
+                level[v] = 0;
+                paths[v] = 1;
+            } else {
+                if (level[v] != ORC_INF) continue;
+                level[v] = (uint32_t)msg[v].a;
+                paths[v] = msg[v].b;
+            }
+            senders++;
+            for (uint64_t e = off[v]; e < off[v + 1]; ++e) {
+                orc_msg m = {(uint64_t)level[v] + 1, paths[v]};
+                send_gen(&mb, col[e], m);
+            }
+        }
+        uint64_t sent = mb.sent;
+        orc_msg* tm = msg;
+        msg = mb.msg_next;
+        mb.msg_next = tm;
+        uint8_t* th = has;
+        has = mb.has_next;
+        mb.has_next = th;
+        memset(mb.has_next, 0, k);
+        uint64_t receivers = 0;
+        for (uint32_t v = 0; v < n; ++v) receivers += has[v];
+        record(st, cap, s, active, senders, sent, receivers);
+        s++;
+        if (sent == 0) break;
+        if (max_supersteps && s >= max_supersteps) break;
+        active = receivers;
+    }
+    if (supersteps_out) *supersteps_out = s;
+    free(msg);
+    free(has);
+    free(mb.msg_next);
+    free(mb.has_next);
     return ORC_OK;
 }
