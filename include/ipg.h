@@ -220,6 +220,81 @@ ipg_status ipg_sssp_noalloc(const uint64_t* offsets_dev, const uint32_t* columns
                             void* stream);
 
 /*
+ * General combiners (Sec. III, Fig. 1).  The calls below run vertex programs
+ * whose messages are wider than 32 bits and whose combine is not a hardware
+ * atomic, through the hybrid combiner of include/ipg_combiner.cuh: each
+ * mailbox is a flag plus a message slot; the first message takes a per-vertex
+ * lock, stores itself and raises the flag, later ones combine into the slot by
+ * compare-and-swap.  A vertex is active in the next superstep exactly when it
+ * received a message (its flag was raised), as in the Pregel model, whatever
+ * the combined value.  Every superstep record has IPG_STAT_RECEIVERS set: the
+ * receivers are counted exactly, for free, by the first-message path.
+ * A bounded wait inside the combiner that runs out returns IPG_ETIMEOUT.
+ */
+
+/*
+ * ipg_sssp_tree — SSSP that also returns a shortest-path tree.  Each message
+ * is the 64-bit pair (distance, sender id), combined by the lexicographic
+ * minimum, so a vertex keeps the smallest (distance, parent) it ever heard of.
+ * It sends only when its distance drops, so the senders, messages and
+ * superstep count equal ipg_sssp's.
+ *   source      vertex id < n, else IPG_EINVAL;
+ *   dist_out    host, n uint32 (UINT32_MAX = unreachable) — equal to ipg_sssp's;
+ *   parent_out  host, n uint32: for a reached vertex v other than the source,
+ *               the smallest u with an edge u -> v and dist[u] + w(u,v) = dist[v];
+ *               the source's parent is the source; UINT32_MAX if unreached.
+ * A path length that would reach UINT32_MAX returns IPG_EOVERFLOW.
+ */
+ipg_status ipg_sssp_tree(ipg_graph* g, uint32_t source, uint32_t* dist_out, uint32_t* parent_out, ipg_stats* stats);
+ipg_status ipg_sssp_tree_dev(ipg_graph* g, uint32_t source, uint32_t* dist_dev, uint32_t* parent_dev,
+                             ipg_stats* stats, void* stream);
+
+/*
+ * ipg_bfs_paths — number of shortest paths from a source, by breadth-first
+ * levels.  Each message is the 128-bit pair (level, count); the combine keeps
+ * the smallest level and adds the counts of messages at that level.  Every
+ * edge has length 1 (weights are ignored) and is one message, so parallel
+ * edges count as distinct paths.  Counts are exact modulo 2^64.
+ *   source     vertex id < n, else IPG_EINVAL;
+ *   level_out  host, n uint32: hop distance from the source (UINT32_MAX = unreachable);
+ *   paths_out  host, n uint64: shortest paths from the source modulo 2^64 (0 = unreachable).
+ */
+ipg_status ipg_bfs_paths(ipg_graph* g, uint32_t source, uint32_t* level_out, uint64_t* paths_out, ipg_stats* stats);
+ipg_status ipg_bfs_paths_dev(ipg_graph* g, uint32_t source, uint32_t* level_dev, uint64_t* paths_dev,
+                             ipg_stats* stats, void* stream);
+
+/*
+ * ipg_combine_dev — the combination step alone: deliver k messages, message i
+ * to vertex dst[i], into n mailboxes that start empty.
+ *   kind       an ipg_combine_kind (the message size follows from it);
+ *   dst_dev    device, k uint32, each < n (else IPG_EINVAL, nothing is
+ *              written out of bounds);
+ *   msgs_dev   device, k messages of the kind's size, 16-byte aligned for the
+ *              128-bit kind (a (key u64, count u64) pair);
+ *   flags_dev  device, n uint32, out: 1 where the vertex received a message, 0
+ *              elsewhere (cleared by the call);
+ *   mail_dev   device, n messages of the kind's size, out: the combined message
+ *              where flags_dev is 1, untouched elsewhere;
+ *   receivers_out  host, optional: number of vertices that received a message;
+ *   options    IPG_COMBINE_WARP (fold same-destination messages within a warp
+ *              before the mailbox) and/or IPG_COMBINE_NATIVE (IPG_COMBINE_MIN_U64
+ *              only: a hardware 64-bit atomicMin on a slot preset to the maximum
+ *              instead of the hybrid combiner; same result — a comparison point).
+ * Returns after the result is complete on `stream`.  k may be 0.
+ */
+typedef enum {
+    IPG_COMBINE_XOR_U32 = 0,       /* 4-byte messages, bitwise exclusive or */
+    IPG_COMBINE_MIN_U64 = 1,       /* 8-byte messages, minimum */
+    IPG_COMBINE_SUM_U64 = 2,       /* 8-byte messages, sum modulo 2^64 */
+    IPG_COMBINE_MINCOUNT_U128 = 3  /* 16-byte (key, count): smallest key, counts at that key added modulo 2^64 */
+} ipg_combine_kind;
+#define IPG_COMBINE_WARP 1u
+#define IPG_COMBINE_NATIVE 2u
+ipg_status ipg_combine_dev(int kind, uint32_t n, const uint32_t* dst_dev, const void* msgs_dev, uint64_t k,
+                           uint32_t* flags_dev, void* mail_dev, uint64_t* receivers_out, uint32_t options,
+                           void* stream);
+
+/*
  * Serving (not in the paper): a resident set of graphs answering a stream of
  * queries with continuous batching.  Worker threads take the graph whose head
  * query has waited longest (one worker per graph at a time); all of its queued
@@ -290,6 +365,9 @@ void ipg_server_destroy(ipg_server* s);
  *                   pull form (every vertex scans its in-edges, as the paper's
  *                   pull-based CC version does, Sec. VI-C) instead of push form.
  *                   0 = always push.  Default 6.
+ *   "combine_warp"  ipg_sssp_tree / ipg_bfs_paths: 1 = lanes of a warp that send to
+ *                   the same vertex fold their messages first (IPG_COMBINE_WARP),
+ *                   0 = every message goes to the mailbox.  Default 0.
  * Unknown names or invalid values return IPG_EINVAL.  Set knobs between calls,
  * not while a call runs.
  */

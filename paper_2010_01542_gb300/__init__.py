@@ -448,6 +448,87 @@ __all__ += ["ipg_graph_create_batch", "ipg_graph_instances", "ipg_hashmin_cc_bat
 
 
 # ---------------------------------------------------------------------------------------
+# general combiners (Sec. III, Fig. 1): wider messages through the hybrid combiner
+
+IPG_COMBINE_XOR_U32, IPG_COMBINE_MIN_U64, IPG_COMBINE_SUM_U64, IPG_COMBINE_MINCOUNT_U128 = 0, 1, 2, 3
+IPG_COMBINE_WARP = 1
+IPG_COMBINE_NATIVE = 2
+_COMBINE_SIZE = {IPG_COMBINE_XOR_U32: 4, IPG_COMBINE_MIN_U64: 8, IPG_COMBINE_SUM_U64: 8, IPG_COMBINE_MINCOUNT_U128: 16}
+
+
+def _fn(name, argtypes):
+    fn = getattr(load_library(), name)
+    fn.argtypes = argtypes
+    fn.restype = ctypes.c_int
+    return fn
+
+
+_VP, _U32, _U64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+_PSTATS = ctypes.POINTER(_CStatsBuf)
+
+
+def ipg_sssp_tree(g: Graph, source: int, stats_flags: int = 0, stats_cap: int = 1 << 16):
+    """SSSP with its shortest-path tree into host arrays.  Returns (dist, parent, supersteps, stats)."""
+    n = ipg_graph_info(g)["n"]
+    dist = np.empty(n, dtype=np.uint32)
+    parent = np.empty(n, dtype=np.uint32)
+    fn = _fn("ipg_sssp_tree", [_VP, _U32, _VP, _VP, _PSTATS])
+    count, stats = _run(fn, (g.handle, source, dist.ctypes.data if n else None, parent.ctypes.data if n else None),
+                        stats_flags, stats_cap)
+    return dist, parent, count, stats
+
+
+def ipg_sssp_tree_dev(g: Graph, source: int, dist_dev, parent_dev, stats_flags: int = 0, stats_cap: int = 1 << 16,
+                      stream=None):
+    n = ipg_graph_info(g)["n"]
+    fn = _fn("ipg_sssp_tree_dev", [_VP, _U32, _VP, _VP, _PSTATS, _VP])
+    return _run_dev(fn, (g.handle, source, _dev_ptr(dist_dev, 4, n, "dist"), _dev_ptr(parent_dev, 4, n, "parent")),
+                    stats_flags, stats_cap, stream)
+
+
+def ipg_bfs_paths(g: Graph, source: int, stats_flags: int = 0, stats_cap: int = 1 << 16):
+    """Shortest-path counts from `source` into host arrays.  Returns (level, paths, supersteps, stats)."""
+    n = ipg_graph_info(g)["n"]
+    level = np.empty(n, dtype=np.uint32)
+    paths = np.empty(n, dtype=np.uint64)
+    fn = _fn("ipg_bfs_paths", [_VP, _U32, _VP, _VP, _PSTATS])
+    count, stats = _run(fn, (g.handle, source, level.ctypes.data if n else None, paths.ctypes.data if n else None),
+                        stats_flags, stats_cap)
+    return level, paths, count, stats
+
+
+def ipg_bfs_paths_dev(g: Graph, source: int, level_dev, paths_dev, stats_flags: int = 0, stats_cap: int = 1 << 16,
+                      stream=None):
+    n = ipg_graph_info(g)["n"]
+    fn = _fn("ipg_bfs_paths_dev", [_VP, _U32, _VP, _VP, _PSTATS, _VP])
+    return _run_dev(fn, (g.handle, source, _dev_ptr(level_dev, 4, n, "level"), _dev_ptr(paths_dev, 8, n, "paths")),
+                    stats_flags, stats_cap, stream)
+
+
+def ipg_combine_dev(kind: int, n: int, dst_dev, msgs_dev, flags_dev, mail_dev, options: int = 0, stream=None) -> int:
+    """Deliver messages msgs_dev[i] to dst_dev[i] into n empty mailboxes (CUDA tensors:
+    dst int32/uint32 [k]; msgs of the kind's size — int32 [k], int64 [k] or int64 [k, 2];
+    flags int32 [n]; mail like msgs with n rows).  Returns the number of receivers."""
+    size = _COMBINE_SIZE.get(kind, 8)  # an unknown kind is left to the library to reject
+    k = 0 if dst_dev is None else dst_dev.numel()
+    width = 2 if size == 16 else 1
+    esize = 4 if size == 4 else 8
+    if msgs_dev is not None and msgs_dev.numel() < k * width:
+        raise ValueError("msgs has fewer entries than dst")
+    fn = _fn("ipg_combine_dev", [ctypes.c_int, _U32, _VP, _VP, _U64, _VP, _VP, ctypes.POINTER(_U64), _U32, _VP])
+    recv = ctypes.c_uint64()
+    _check(fn(kind, n, _dev_ptr(dst_dev, 4, k, "dst"), _dev_ptr(msgs_dev, esize, k * width, "msgs"), k,
+              _dev_ptr(flags_dev, 4, n, "flags"), _dev_ptr(mail_dev, esize, n * width, "mail"), ctypes.byref(recv),
+              options, _stream_ptr(stream)))
+    return int(recv.value)
+
+
+__all__ += ["ipg_sssp_tree", "ipg_sssp_tree_dev", "ipg_bfs_paths", "ipg_bfs_paths_dev", "ipg_combine_dev",
+            "IPG_COMBINE_XOR_U32", "IPG_COMBINE_MIN_U64", "IPG_COMBINE_SUM_U64", "IPG_COMBINE_MINCOUNT_U128",
+            "IPG_COMBINE_WARP", "IPG_COMBINE_NATIVE"]
+
+
+# ---------------------------------------------------------------------------------------
 # serving
 
 IPG_Q_SSSP, IPG_Q_HASHMIN, IPG_Q_PAGERANK = 0, 1, 2

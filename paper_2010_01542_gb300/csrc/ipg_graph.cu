@@ -504,6 +504,7 @@ void release_workspace(ipg_graph* g) {
     f(g->val);
     f(g->sval);
     batch_free(g);
+    generic_free(g);
 }
 
 static void free_graph(ipg_graph* g) {
@@ -549,6 +550,7 @@ static void free_graph(ipg_graph* g) {
     f(g->inst_msgs);
     delete[] g->inst_base_host;
     batch_free(g);
+    generic_free(g);
     if (g->h_counters) cudaFreeHost(g->h_counters);
     g->timer.destroy();
     if (g->stream) cudaStreamDestroy(g->stream);
@@ -780,6 +782,11 @@ ipg_status ipg_set_tuning(const char* name, int64_t value) {
         tuning().pull_divisor = value;
         return IPG_OK;
     }
+    if (!strcmp(name, "combine_warp")) {
+        if (value != 0 && value != 1) return set_error(IPG_EINVAL, "ipg_set_tuning: combine_warp must be 0 or 1");
+        tuning().combine_warp = value;
+        return IPG_OK;
+    }
     return set_error(IPG_EINVAL, "ipg_set_tuning: unknown knob '%s'", name);
 }
 
@@ -787,6 +794,10 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value) {
     if (!name || !value) return set_error(IPG_EINVAL, "ipg_get_tuning: NULL argument");
     if (!strcmp(name, "pull_divisor")) {
         *value = tuning().pull_divisor;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "combine_warp")) {
+        *value = tuning().combine_warp;
         return IPG_OK;
     }
     return set_error(IPG_EINVAL, "ipg_get_tuning: unknown knob '%s'", name);

@@ -129,6 +129,7 @@ struct ipg_graph {
     ipg::PushCounters* h_counters = nullptr;  // pinned host mirror
 
     void* batch = nullptr;          // batched-SSSP workspace (ipg_batch.cu)
+    void* generic = nullptr;        // general-combiner workspace (ipg_generic.cu)
 
     // graphs created by ipg_graph_create_batch: instance i owns caller ids
     // [inst_base[i], inst_base[i+1])
@@ -151,10 +152,18 @@ int sm_count_of(int dev);
 // in ipg_graph.cu: shared by create and create_batch
 ipg_status create_graph(const uint64_t* offsets, const uint32_t* columns, const uint32_t* weights, uint32_t n,
                         uint64_t m, int directed, cudaStream_t user_stream, bool from_device, ipg_graph** out);
+// in ipg_push.cu: the frontier's out-degree prefix, row starts and (if val is not
+// NULL) value snapshot, and the merge-path split of (frontier rows + their edges)
+// into tiles of kFrontierTile items; edges and tiles land in g->counters
+constexpr uint32_t kFrontierTile = 2048;
+ipg_status frontier_prepare(ipg_graph* g, const uint32_t* F, uint32_t f, const uint32_t* val, cudaStream_t st);
+ipg_status frontier_partition(ipg_graph* g, uint32_t f, cudaStream_t st);
 // in ipg_batch.cu
 void batch_free(ipg_graph* g);
 ipg_status sssp_batch_run(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_dev,
                           uint32_t* supersteps_out, cudaStream_t st);
+// in ipg_generic.cu
+void generic_free(ipg_graph* g);
 // caller ids -> internal ids, in place on the device
 ipg_status map_to_internal(ipg_graph* g, uint32_t* ids, uint32_t k, cudaStream_t st);
 // in ipg_pull_min.cu
@@ -163,6 +172,7 @@ ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, const uint32_t
 // process-wide tuning knobs (ipg_set_tuning)
 struct Tuning {
     long long pull_divisor = 6;  // pull when a superstep's messages reach m / pull_divisor; 0 = never
+    long long combine_warp = 0;  // general combiners: fold same-destination messages within a warp first
 };
 Tuning& tuning();
 // stats helpers

@@ -38,7 +38,7 @@ constexpr int kFrItems = 8;
 constexpr uint32_t kFrBlock = kFrThreads * kFrItems;
 constexpr int kScanThreads = 1024;
 constexpr int kPushThreads = 256;
-constexpr uint32_t kPushTile = 2048;
+constexpr uint32_t kPushTile = kFrontierTile;
 
 enum Kind { kHashmin = 0, kSssp = 1 };
 
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kFrThreads) fr_write_kernel(
             uint32_t u = F[i];
             st[q] = off[u];
             deg[q] = off[u + 1] - st[q];
-            fval[i] = val[u];
+            if (val) fval[i] = val[u];
         }
         local += deg[q];
     }
@@ -457,7 +457,6 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
     if (timing) IPG_TRY(ensure_events_push(3, &ev));
     const int sms = sm_count(g->device);
     const unsigned relax_grid = (unsigned)sms * 6;
-    const unsigned part_grid = (unsigned)sms * 2;
 
     IPG_CUDA(cudaMemsetAsync(g->stamp, 0, sizeof(uint32_t) * n, st));
     if (recv) IPG_CUDA(cudaMemsetAsync(g->rstamp, 0, sizeof(uint32_t) * n, st));
@@ -482,13 +481,8 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
     if (per_inst)
         for (uint32_t i = 0; i < ninst; ++i) inst_supersteps[i] = 1;
     for (;;) {
-        const uint32_t nb = (f + kFrBlock - 1) / kFrBlock;
         if (timing) IPG_CUDA(cudaEventRecord(ev[0], st));
-        fr_reduce_kernel<<<nb, kFrThreads, 0, st>>>(g->frontier[cur], f, g->off, g->block_sums);
-        fr_scan_kernel<<<1, kScanThreads, 0, st>>>(g->block_sums, nb, f, g->fr_prefix, g->counters);
-        fr_write_kernel<<<nb, kFrThreads, 0, st>>>(g->frontier[cur], f, g->off, val, g->block_sums, g->fr_prefix,
-                                                   g->fr_rowstart, g->fr_val);
-        IPG_CUDA(cudaGetLastError());
+        IPG_TRY(frontier_prepare(g, g->frontier[cur], f, val, st));
         if (per_inst) {
             IPG_CUDA(cudaMemsetAsync(g->inst_msgs, 0, sizeof(unsigned long long) * ninst, st));
             const size_t shm = ninst <= 2048 ? sizeof(unsigned long long) * ninst : 0;
@@ -514,8 +508,7 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
             IPG_TRY(pull_min_superstep(g, kind == kSssp, recv, g->frontier[cur], g->fr_val, f, val,
                                        g->frontier[cur ^ 1], st, timing ? ev[1] : nullptr));
         } else {
-            push_partition_kernel<<<part_grid, 256, 0, st>>>(g->fr_prefix, f, g->counters, g->push_tile_row);
-            IPG_CUDA(cudaGetLastError());
+            IPG_TRY(frontier_partition(g, f, st));
             if (timing) IPG_CUDA(cudaEventRecord(ev[1], st));
             relax_dispatch(kind, recv, relax_grid, st, g, val, g->frontier[cur ^ 1], f, s + 1);
             IPG_CUDA(cudaGetLastError());
@@ -572,6 +565,23 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
 }
 
 }  // namespace
+
+ipg_status frontier_prepare(ipg_graph* g, const uint32_t* F, uint32_t f, const uint32_t* val, cudaStream_t st) {
+    const uint32_t nb = (f + kFrBlock - 1) / kFrBlock;
+    fr_reduce_kernel<<<nb, kFrThreads, 0, st>>>(F, f, g->off, g->block_sums);
+    fr_scan_kernel<<<1, kScanThreads, 0, st>>>(g->block_sums, nb, f, g->fr_prefix, g->counters);
+    fr_write_kernel<<<nb, kFrThreads, 0, st>>>(F, f, g->off, val, g->block_sums, g->fr_prefix, g->fr_rowstart,
+                                               g->fr_val);
+    IPG_CUDA(cudaGetLastError());
+    return IPG_OK;
+}
+
+ipg_status frontier_partition(ipg_graph* g, uint32_t f, cudaStream_t st) {
+    push_partition_kernel<<<(unsigned)sm_count(g->device) * 2, 256, 0, st>>>(g->fr_prefix, f, g->counters,
+                                                                            g->push_tile_row);
+    IPG_CUDA(cudaGetLastError());
+    return IPG_OK;
+}
 
 ipg_status ensure_push_workspace(ipg_graph* g, bool receivers) {
     const uint32_t n = g->n;

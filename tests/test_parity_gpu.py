@@ -205,7 +205,9 @@ def test_tuning_knobs(ipg):
         ipg.ipg_set_tuning("no_such_knob", 1)
     with pytest.raises(ipg.IpgError):
         ipg.ipg_set_tuning("pull_divisor", -1)
-
+    assert ipg.ipg_get_tuning("combine_warp") in (0, 1)
+    with pytest.raises(ipg.IpgError):
+        ipg.ipg_set_tuning("combine_warp", 2)
 
 
 def test_errors(ipg, direction):
