@@ -787,6 +787,21 @@ ipg_status ipg_set_tuning(const char* name, int64_t value) {
         tuning().combine_warp = value;
         return IPG_OK;
     }
+    if (!strcmp(name, "pr_engine")) {
+        if (value != 0 && value != 1) return set_error(IPG_EINVAL, "ipg_set_tuning: pr_engine must be 0 or 1");
+        tuning().pr_engine = value;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "pr_threads")) {
+        if (value != 256 && value != 512) return set_error(IPG_EINVAL, "ipg_set_tuning: pr_threads must be 256 or 512");
+        tuning().pr_threads = value;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "pr_carveout")) {
+        if (value < -1 || value > 100) return set_error(IPG_EINVAL, "ipg_set_tuning: pr_carveout must be in [-1, 100]");
+        tuning().pr_carveout = value;
+        return IPG_OK;
+    }
     return set_error(IPG_EINVAL, "ipg_set_tuning: unknown knob '%s'", name);
 }
 
@@ -798,6 +813,18 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value) {
     }
     if (!strcmp(name, "combine_warp")) {
         *value = tuning().combine_warp;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "pr_engine")) {
+        *value = tuning().pr_engine;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "pr_threads")) {
+        *value = tuning().pr_threads;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "pr_carveout")) {
+        *value = tuning().pr_carveout;
         return IPG_OK;
     }
     return set_error(IPG_EINVAL, "ipg_get_tuning: unknown knob '%s'", name);

@@ -173,6 +173,9 @@ ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, const uint32_t
 struct Tuning {
     long long pull_divisor = 6;  // pull when a superstep's messages reach m / pull_divisor; 0 = never
     long long combine_warp = 0;  // general combiners: fold same-destination messages within a warp first
+    long long pr_threads = 256;  // PageRank pull kernel: threads per CTA (256 or 512)
+    long long pr_carveout = -1;  // PageRank pull kernel: shared-memory carveout percent (-1 = smallest)
+    long long pr_engine = 0;     // PageRank pull kernel: 0 staged messages, 1 direct (registers)
 };
 Tuning& tuning();
 // stats helpers

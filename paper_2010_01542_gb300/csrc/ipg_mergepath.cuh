@@ -56,11 +56,16 @@ struct MinU32 {
     static __device__ __forceinline__ uint32_t combine(uint32_t a, uint32_t b) { return a < b ? a : b; }
 };
 
+// Staging of one tile.  A tile has R row ends and E edges with R + E <= kTile,
+// so the relative row ends (R + 1 words) and the padded messages (E + E/32
+// words) share one buffer: end = buf, val = buf + R + 1.  Keeping the staging
+// small leaves more of the SM's unified L1/shared array to the L1 cache, which
+// holds the most gathered messages.
 template <int kThreads, int kItems, typename T>
 struct MpShared {
+    static_assert(sizeof(T) == sizeof(uint32_t), "messages share the row-end buffer");
     static constexpr uint32_t kTile = kThreads * kItems;
-    uint32_t end[kTile + 1];
-    T val[kTile + kTile / 32];
+    uint32_t buf[kTile + kTile / 32 + 2];
     T wsum[kThreads / 32];
     int wflag[kThreads / 32];
     unsigned long long first_start;
@@ -95,6 +100,52 @@ __device__ __forceinline__ uint32_t mp_rel_end(const uint64_t* __restrict__ off,
     return rel < (uint64_t)g.E + 1 ? (uint32_t)rel : g.E + 1;
 }
 
+// Steps 3-4 for one thread of the tile: run is the partial of the thread's last
+// (unfinished) row, first_row / first_val the first row that ended in the
+// thread's slice (-1 if none) and its partial without carry-in; row0_earlier
+// says that row 0 of the tile began in an earlier tile.  Contains one
+// __syncthreads().
+template <int kThreads, class Op, class Emit>
+__device__ __forceinline__ void mp_scan_finish(typename Op::T run, int first_row, typename Op::T first_val,
+                                               const MpGeom& g, bool row0_earlier, typename Op::T* wsum, int* wflag,
+                                               uint64_t tile, typename Op::T* __restrict__ tile_head,
+                                               typename Op::T* __restrict__ tile_tail, Emit& emit, int tid) {
+    typedef typename Op::T T;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+    // segmented inclusive scan of (row ended, partial): (f, v) then (g, w) -> (f|g, g ? w : v + w)
+    T v = run;
+    int f = first_row >= 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T vu = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        const int fu = __shfl_up_sync(0xFFFFFFFFu, f, o);
+        if (lane >= o) {
+            if (!f) v = Op::combine(vu, v);
+            f |= fu;
+        }
+    }
+    if (lane == 31) {
+        wsum[warp] = v;
+        wflag[warp] = f;
+    }
+    __syncthreads();
+    T wc = Op::identity();
+    for (int q = 0; q < warp; ++q) wc = wflag[q] ? wsum[q] : Op::combine(wc, wsum[q]);
+    const T incl = f ? v : Op::combine(wc, v);
+    T excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
+    if (lane == 0) excl = wc;
+    if (tid == kThreads - 1) tile_tail[tile] = incl;  // partial of row i1 inside this tile
+    // the slice's first finished row, with the carry-in
+    if (first_row >= 0) {
+        const T tot = Op::combine(excl, first_val);
+        if (row0_earlier)
+            tile_head[tile] = tot;  // row i0 began in an earlier tile
+        else
+            emit(g.i0 + (uint32_t)first_row, tot);
+    }
+}
+
 // Steps 2-4 on a staged tile: end[0..R] (relative row ends), val[mp_pad(k)] for
 // k < E, and first_start = offset of row i0, all visible to every thread.
 // Contains one __syncthreads().
@@ -106,8 +157,6 @@ __device__ __forceinline__ void mp_reduce(const uint32_t* end, const typename Op
     typedef typename Op::T T;
     static_assert(kThreads * kItems == (int)kMpTile, "tiles share one partition");
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int warp = tid >> 5;
     // walk this thread's slice once
     const uint32_t items = g.R + g.E;
     const uint32_t ds = min((uint32_t)tid * kItems, items);
@@ -143,37 +192,8 @@ __device__ __forceinline__ void mp_reduce(const uint32_t* end, const typename Op
             }
         }
     }
-    // segmented inclusive scan of (row ended, partial): (f, v) then (g, w) -> (f|g, g ? w : v + w)
-    T v = run;
-    int f = first_row >= 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const T vu = __shfl_up_sync(0xFFFFFFFFu, v, o);
-        const int fu = __shfl_up_sync(0xFFFFFFFFu, f, o);
-        if (lane >= o) {
-            if (!f) v = Op::combine(vu, v);
-            f |= fu;
-        }
-    }
-    if (lane == 31) {
-        wsum[warp] = v;
-        wflag[warp] = f;
-    }
-    __syncthreads();
-    T wc = Op::identity();
-    for (int q = 0; q < warp; ++q) wc = wflag[q] ? wsum[q] : Op::combine(wc, wsum[q]);
-    const T incl = f ? v : Op::combine(wc, v);
-    T excl = __shfl_up_sync(0xFFFFFFFFu, incl, 1);
-    if (lane == 0) excl = wc;
-    if (tid == kThreads - 1) tile_tail[tile] = incl;  // partial of row i1 inside this tile
-    // the slice's first finished row, with the carry-in
-    if (first_row >= 0) {
-        const T tot = Op::combine(excl, first_val);
-        if (first_row == 0 && first_start < g.j0)
-            tile_head[tile] = tot;  // row i0 began in an earlier tile
-        else
-            emit(g.i0 + (uint32_t)first_row, tot);
-    }
+    mp_scan_finish<kThreads, Op>(run, first_row, first_val, g, first_row == 0 && first_start < g.j0, wsum, wflag,
+                                 tile, tile_head, tile_tail, emit, tid);
 }
 
 // Processes tile `tile` with plain staging.  gather.template stage<kThreads, kItems>
@@ -185,15 +205,123 @@ __device__ __forceinline__ void mp_tile(MpShared<kThreads, kItems, typename Op::
                                         const uint32_t* __restrict__ tile_row, uint64_t tile,
                                         typename Op::T* __restrict__ tile_head,
                                         typename Op::T* __restrict__ tile_tail, Gather& gather, Emit& emit) {
+    typedef typename Op::T T;
     const MpGeom g = mp_geom(tile_row, tile, n, m);
     const int tid = threadIdx.x;
+    uint32_t* end = sh.buf;
+    T* val = reinterpret_cast<T*>(sh.buf + g.R + 1);
     __syncthreads();  // shared memory of the previous tile is free
-    for (uint32_t k = tid; k <= g.R; k += kThreads) sh.end[k] = mp_rel_end(off, g, k, n);
+    for (uint32_t k = tid; k <= g.R; k += kThreads) end[k] = mp_rel_end(off, g, k, n);
     if (tid == 0) sh.first_start = g.i0 < n ? off[g.i0] : m;
-    gather.template stage<kThreads, kItems>(g.j0, g.E, tid, sh.val);
+    gather.template stage<kThreads, kItems>(g.j0, g.E, tid, val);
     __syncthreads();
-    mp_reduce<kThreads, kItems, Op>(sh.end, sh.val, g, sh.first_start, sh.wsum, sh.wflag, tile, tile_head, tile_tail,
-                                    emit);
+    mp_reduce<kThreads, kItems, Op>(end, val, g, sh.first_start, sh.wsum, sh.wflag, tile, tile_head, tile_tail, emit);
+}
+
+// ---------------------------------------------------------------------------
+// Direct variant: no message staging.  The tile's row ends are marked in a
+// kMpTile-bit mask (row k of the tile ends at merge item rel_end(k) + k); each
+// thread finds the rows before its slice by a popcount prefix of the mask and
+// has msg.template fetch<kItems>() load the messages of its own kItems items
+// straight into registers.  Walk, scan and combine order are those of the
+// staged engine, so results are bit-identical to it.  Shared memory is under
+// 1 KB per CTA, which leaves nearly all of the SM's unified L1/shared array to
+// the L1 cache: the gathers of the most-connected senders hit there.
+template <int kThreads, typename T>
+struct MpDirectShared {
+    uint32_t bits[kMpTile / 32];  // bit p: merge item p is a row end
+    uint32_t pre[kMpTile / 32];   // exclusive prefix of the words' popcounts
+    T wsum[kThreads / 32];
+    int wflag[kThreads / 32];
+};
+
+template <int kThreads, typename T>
+__device__ __forceinline__ void mp_direct_init(MpDirectShared<kThreads, T>& sh) {
+    for (uint32_t w = threadIdx.x; w < kMpTile / 32; w += kThreads) sh.bits[w] = 0;
+}
+
+// msg.template fetch<kItems>(j0, emask, eidx, x): for every q with bit q of
+// emask set, x[q] = message of edge j0 + eidx[q].  emask is 0 when the tile
+// has no edges.  The mask must be zero on entry (mp_direct_init, and every call
+// leaves it zeroed).  Contains four __syncthreads().
+template <int kThreads, int kItems, class Op, class Msg, class Emit>
+__device__ __forceinline__ void mp_tile_direct(MpDirectShared<kThreads, typename Op::T>& sh,
+                                               const uint64_t* __restrict__ off, uint32_t n, uint64_t m,
+                                               const uint32_t* __restrict__ tile_row, uint64_t tile,
+                                               typename Op::T* __restrict__ tile_head,
+                                               typename Op::T* __restrict__ tile_tail, const Msg& msg, Emit& emit) {
+    typedef typename Op::T T;
+    static_assert(kThreads * kItems == (int)kMpTile, "tiles share one partition");
+    static_assert(32 % kItems == 0, "a thread's items lie in one mask word");
+    const MpGeom g = mp_geom(tile_row, tile, n, m);
+    const int tid = threadIdx.x;
+    const uint32_t items = g.R + g.E;
+    __syncthreads();  // the previous tile has read the mask and its warp partials
+    for (uint32_t k = tid; k < g.R; k += kThreads) {
+        const uint32_t p = (uint32_t)(__ldg(off + g.i0 + k + 1) - g.j0) + k;
+        if (p < items) atomicOr(&sh.bits[p >> 5], 1u << (p & 31));
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const uint32_t c0 = __popc(sh.bits[tid]), c1 = __popc(sh.bits[tid + 32]);
+        uint32_t a = c0, b = c1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t ua = __shfl_up_sync(0xFFFFFFFFu, a, o);
+            const uint32_t ub = __shfl_up_sync(0xFFFFFFFFu, b, o);
+            if (tid >= o) {
+                a += ua;
+                b += ub;
+            }
+        }
+        const uint32_t tot0 = __shfl_sync(0xFFFFFFFFu, a, 31);
+        sh.pre[tid] = a - c0;
+        sh.pre[tid + 32] = tot0 + b - c1;
+    }
+    __syncthreads();
+    // this thread's slice [ds, ds + nval) of the tile's merge items
+    const uint32_t ds = min((uint32_t)tid * kItems, items);
+    const uint32_t nval = min(ds + kItems, items) - ds;
+    uint32_t ends = 0, i = 0, j = 0;
+    if (nval) {
+        const uint32_t word = sh.bits[ds >> 5];
+        const uint32_t sft = ds & 31;
+        ends = (word >> sft) & ((1u << nval) - 1u);
+        i = sh.pre[ds >> 5] + __popc(word & ((1u << sft) - 1u));
+        j = ds - i;
+    }
+    uint32_t emask = 0, eidx[kItems];
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+        eidx[q] = j + q - __popc(ends & ((1u << q) - 1u));
+        if ((uint32_t)q < nval && !((ends >> q) & 1u)) emask |= 1u << q;
+    }
+    T x[kItems];
+    if (g.E) msg.template fetch<kItems>(g.j0, emask, eidx, x);
+    T run = Op::identity(), first_val = Op::identity();
+    int first_row = -1;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+        if ((uint32_t)q < nval) {
+            if ((ends >> q) & 1u) {
+                if (first_row < 0) {
+                    first_row = (int)i;
+                    first_val = run;
+                } else {
+                    emit(g.i0 + i, run);
+                }
+                run = Op::identity();
+                ++i;
+            } else {
+                run = Op::combine(run, x[q]);
+            }
+        }
+    }
+    const bool row0_earlier = first_row == 0 && __ldg(off + g.i0) < g.j0;
+    mp_scan_finish<kThreads, Op>(run, first_row, first_val, g, row0_earlier, sh.wsum, sh.wflag, tile, tile_head,
+                                 tile_tail, emit, tid);
+    // every read of the mask happened before the scan's barrier
+    for (uint32_t w = tid; w < kMpTile / 32; w += kThreads) sh.bits[w] = 0;
 }
 
 // Tile t's first row, if it began in an earlier tile and ends in t: returns the
@@ -217,5 +345,13 @@ ipg_status mp_partition(const uint64_t* off, uint32_t n, uint64_t m, uint64_t ti
                         cudaStream_t st);
 
 inline uint64_t mp_tile_count(uint32_t n, uint64_t m) { return ((uint64_t)n + m + kMpTile - 1) / kMpTile; }
+
+// Persistent grid for a pull kernel: the SM's unified L1/shared array is split
+// with the smallest shared-memory carveout that still holds the most resident
+// CTAs (carve < 0), or with carve percent, on every kernel of `kernels`; the
+// grid is every resident CTA, at most `tiles`.  The L1 left over caches the
+// gathered messages of the most-connected senders.
+ipg_status pull_grid(const void* const* kernels, int nkernels, int threads, int device, uint64_t tiles, int carve,
+                     unsigned* grid);
 
 }  // namespace ipg

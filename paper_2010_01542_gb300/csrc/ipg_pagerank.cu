@@ -48,10 +48,33 @@ ipg_status mp_partition(const uint64_t* off, uint32_t n, uint64_t m, uint64_t ti
     return IPG_OK;
 }
 
-namespace {
+ipg_status pull_grid(const void* const* kernels, int nkernels, int threads, int device, uint64_t tiles, int carve,
+                     unsigned* grid) {
+    if (carve < 0) {
+        cudaFuncAttributes fa;
+        IPG_CUDA(cudaFuncGetAttributes(&fa, kernels[0]));
+        for (int i = 0; i < nkernels; ++i)
+            IPG_CUDA(cudaFuncSetAttribute(kernels[i], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        int per_sm = 0, smem_sm = 0;
+        IPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernels[0], threads, 0));
+        IPG_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+        // 1 KB per resident CTA is reserved by the runtime
+        const double need = (double)per_sm * ((double)fa.sharedSizeBytes + 1024.0);
+        carve = (int)(100.0 * need / (smem_sm > 0 ? smem_sm : 1)) + 1;
+        if (carve > 100) carve = 100;
+    }
+    for (int i = 0; i < nkernels; ++i)
+        IPG_CUDA(cudaFuncSetAttribute(kernels[i], cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+    int blocks = 0;
+    IPG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernels[0], threads, 0));
+    if (blocks < 1) blocks = 1;
+    uint64_t gr = (uint64_t)sm_count_of(device) * blocks;
+    if (gr > tiles) gr = tiles;
+    *grid = (unsigned)(gr ? gr : 1);
+    return IPG_OK;
+}
 
-constexpr int kPrThreads = 256;
-constexpr int kPrItems = 8;
+namespace {
 
 __global__ void inv_outdeg_kernel(const uint64_t* __restrict__ off, uint32_t n, float* __restrict__ inv) {
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -77,7 +100,7 @@ __global__ void unpermute_kernel(const float* __restrict__ in, const uint32_t* _
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) out[v] = in[inv[v]];
 }
 
-// message of in-edge j0 + k: the sender's outbox (source ids streamed, outboxes gathered)
+// staged engine: the message of in-edge j0 + k (source ids streamed, outboxes gathered)
 struct PrGather {
     const uint32_t* __restrict__ src;
     const float* __restrict__ box;
@@ -97,6 +120,24 @@ struct PrGather {
     }
 };
 
+// direct engine: messages of a thread's in-edges j0 + eidx[q], the senders' outboxes.  The
+// source ids are streamed (read once, evict-first), the outboxes gathered
+// through L1.  Every load is issued unconditionally so that all of them are in
+// flight at once; an item that is not an edge loads edge j0 (the tile has at
+// least one edge when this is called) and its value is ignored.
+struct PrMsg {
+    const uint32_t* __restrict__ src;
+    const float* __restrict__ box;
+    template <int kItems>
+    __device__ __forceinline__ void fetch(uint64_t j0, uint32_t emask, const uint32_t* eidx, float* x) const {
+        uint32_t u[kItems];
+#pragma unroll
+        for (int q = 0; q < kItems; ++q) u[q] = __ldcs(src + j0 + ((emask >> q) & 1u ? eidx[q] : 0u));
+#pragma unroll
+        for (int q = 0; q < kItems; ++q) x[q] = __ldg(box + u[q]);
+    }
+};
+
 // rank = 0.15/N + 0.85 * sum; outbox = rank / outdeg; the rank itself only in the last superstep
 template <bool kFinal>
 struct PrEmit {
@@ -111,17 +152,30 @@ struct PrEmit {
     }
 };
 
-template <bool kFinal>
-__global__ void __launch_bounds__(kPrThreads) pr_pull_kernel(
+// kThreads threads per CTA, each walking 2048 / kThreads merge items of a tile;
+// kDirect selects the direct engine (messages loaded into registers) over the
+// staged one (messages staged in shared memory).  Both sum in the same order.
+template <bool kFinal, int kThreads, bool kDirect>
+__global__ void __launch_bounds__(kThreads) pr_pull_kernel(
     const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ csc_src, const float* __restrict__ box_in,
     const float* __restrict__ inv_outdeg, float* __restrict__ box_out, float* __restrict__ rank_out,
     const uint32_t* __restrict__ tile_row, float* __restrict__ tile_head, float* __restrict__ tile_tail,
     uint64_t tiles, uint32_t n, uint64_t m, float base, float damp) {
-    __shared__ MpShared<kPrThreads, kPrItems, float> sh;
-    PrGather gather{csc_src, box_in};
+    constexpr int kItems = (int)kMpTile / kThreads;
     PrEmit<kFinal> emit{inv_outdeg, box_out, rank_out, base, damp};
-    for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x)
-        mp_tile<kPrThreads, kPrItems, SumF32>(sh, csc_off, n, m, tile_row, tile, tile_head, tile_tail, gather, emit);
+    if (kDirect) {
+        __shared__ MpDirectShared<kThreads, float> sh;
+        mp_direct_init(sh);
+        const PrMsg msg{csc_src, box_in};
+        for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x)
+            mp_tile_direct<kThreads, kItems, SumF32>(sh, csc_off, n, m, tile_row, tile, tile_head, tile_tail, msg,
+                                                     emit);
+    } else {
+        __shared__ MpShared<kThreads, kItems, float> sh;
+        PrGather gather{csc_src, box_in};
+        for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x)
+            mp_tile<kThreads, kItems, SumF32>(sh, csc_off, n, m, tile_row, tile, tile_head, tile_tail, gather, emit);
+    }
 }
 
 // rows whose in-edges span several tiles: the partial sums, added in tile order in double precision
@@ -146,7 +200,6 @@ __global__ void pr_fixup_kernel(const uint64_t* __restrict__ csc_off, const uint
 ipg_status pr_prepare(ipg_graph* g, cudaStream_t st) {
     IPG_TRY(ensure_csc(g, st));
     const uint32_t n = g->n;
-    const uint64_t m = g->m;
     if (!g->inv_outdeg) {
         IPG_CUDA(cudaMalloc(&g->inv_outdeg, sizeof(float) * (n ? n : 1)));
         inv_outdeg_kernel<<<grid_cap(n), 256, 0, st>>>(g->off, n, g->inv_outdeg);
@@ -159,17 +212,56 @@ ipg_status pr_prepare(ipg_graph* g, cudaStream_t st) {
     return IPG_OK;
 }
 
-unsigned pr_grid(ipg_graph* g) {
-    static int per_sm = 0;
-    if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pr_pull_kernel<false>, kPrThreads, 0) !=
-                cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
+// Launch shape of the pull kernel: engine (knob pr_engine: 0 staged, 1 direct),
+// threads per CTA (knob pr_threads: 256 or 512), the shared-memory carveout
+// (knob pr_carveout: -1 = the smallest that keeps full occupancy, leaving the
+// rest of the unified array to L1; 0..100 = that percentage) and the grid
+// (every resident CTA, persistent over tiles).  Only speed depends on it.
+struct PrLaunch {
+    int threads = 256;
+    bool direct = false;
+    unsigned grid = 1;
+};
+
+template <bool kFinal>
+static const void* pr_kernel_for(int threads, bool direct) {
+    if (direct)
+        return threads == 512 ? reinterpret_cast<const void*>(&pr_pull_kernel<kFinal, 512, true>)
+                              : reinterpret_cast<const void*>(&pr_pull_kernel<kFinal, 256, true>);
+    return threads == 512 ? reinterpret_cast<const void*>(&pr_pull_kernel<kFinal, 512, false>)
+                          : reinterpret_cast<const void*>(&pr_pull_kernel<kFinal, 256, false>);
+}
+
+ipg_status pr_launch_shape(ipg_graph* g, PrLaunch* L) {
+    const Tuning& tu = tuning();
+    L->threads = tu.pr_threads == 512 ? 512 : 256;
+    L->direct = tu.pr_engine == 1;
+    const void* k[2] = {pr_kernel_for<false>(L->threads, L->direct), pr_kernel_for<true>(L->threads, L->direct)};
+    return pull_grid(k, 2, L->threads, g->device, g->pr_tiles, (int)tu.pr_carveout, &L->grid);
+}
+
+template <bool kFinal, int kThreads, bool kDirect>
+static void pr_launch1(const PrLaunch& L, ipg_graph* g, const float* in, float* outb, cudaStream_t st, float base,
+                       float damp) {
+    pr_pull_kernel<kFinal, kThreads, kDirect><<<L.grid, kThreads, 0, st>>>(
+        g->csc_off, g->csc_src, in, g->inv_outdeg, outb, g->pr_rank, g->pr_tile_row, g->pr_head, g->pr_tail,
+        g->pr_tiles, g->n, g->m, base, damp);
+}
+
+template <bool kFinal>
+static void pr_launch(const PrLaunch& L, ipg_graph* g, const float* in, float* outb, cudaStream_t st, float base,
+                      float damp) {
+    if (L.direct) {
+        if (L.threads == 512)
+            pr_launch1<kFinal, 512, true>(L, g, in, outb, st, base, damp);
+        else
+            pr_launch1<kFinal, 256, true>(L, g, in, outb, st, base, damp);
+    } else {
+        if (L.threads == 512)
+            pr_launch1<kFinal, 512, false>(L, g, in, outb, st, base, damp);
+        else
+            pr_launch1<kFinal, 256, false>(L, g, in, outb, st, base, damp);
     }
-    uint64_t grid = (uint64_t)sm_count_of(g->device) * per_sm;
-    if (grid > g->pr_tiles) grid = g->pr_tiles;
-    return (unsigned)(grid ? grid : 1);
 }
 
 }  // namespace
@@ -217,7 +309,8 @@ static ipg_status pagerank_run(ipg_graph* g, uint32_t updates, float* ranks_dev,
             pr_init_kernel<<<grid_cap(n), 256, 0, st>>>(g->inv_outdeg, n, 1.0f / N, g->pr_box[0]);
             IPG_CUDA(cudaGetLastError());
             const uint64_t tiles = g->pr_tiles;
-            const unsigned grid = pr_grid(g);
+            PrLaunch L;
+            IPG_TRY(pr_launch_shape(g, &L));
             int cur = 0;
             for (uint32_t t = 1; t <= updates; ++t) {
                 const bool fin = t == updates;
@@ -225,13 +318,9 @@ static ipg_status pagerank_run(ipg_graph* g, uint32_t updates, float* ranks_dev,
                 float* outb = g->pr_box[cur ^ 1];
                 if (timing) IPG_CUDA(cudaEventRecord(ev[3 * (t - 1)], st));
                 if (fin)
-                    pr_pull_kernel<true><<<grid, kPrThreads, 0, st>>>(g->csc_off, g->csc_src, in, g->inv_outdeg, outb,
-                                                                       g->pr_rank, g->pr_tile_row, g->pr_head,
-                                                                       g->pr_tail, tiles, n, m, base, damp);
+                    pr_launch<true>(L, g, in, outb, st, base, damp);
                 else
-                    pr_pull_kernel<false><<<grid, kPrThreads, 0, st>>>(g->csc_off, g->csc_src, in, g->inv_outdeg,
-                                                                        outb, g->pr_rank, g->pr_tile_row, g->pr_head,
-                                                                        g->pr_tail, tiles, n, m, base, damp);
+                    pr_launch<false>(L, g, in, outb, st, base, damp);
                 IPG_CUDA(cudaGetLastError());
                 if (timing) IPG_CUDA(cudaEventRecord(ev[3 * (t - 1) + 1], st));
                 if (fin)

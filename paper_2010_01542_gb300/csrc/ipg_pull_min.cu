@@ -66,17 +66,31 @@ struct PmGather {
     }
 };
 
+// A strict drop lowers the value and queues the vertex for the next frontier in
+// shared memory; the CTA flushes its queue with one atomic per tile.  Only a
+// row that began in this tile can be emitted here, and it can drop only if it
+// has an in-edge in the tile, so a tile emits at most min(R, E) <= kMpTile / 2
+// drops and the queue never fills; a full queue would append straight to the
+// global frontier.
+constexpr unsigned kPmQueue = kMpTile / 2;
+
 template <bool kRecv>
 struct PmEmit {
     uint32_t* __restrict__ val;
     uint32_t* q;          // shared-memory queue of this tile's new frontier vertices
     unsigned int* qn;     // shared-memory queue length
     unsigned int* nrecv;  // shared-memory receiver count
+    uint32_t* __restrict__ next;
+    PushCounters* ctr;
     __device__ __forceinline__ void operator()(uint32_t row, uint32_t m) const {
         if (kRecv && m != kInf) atomicAdd(nrecv, 1u);
         if (m < val[row]) {
             val[row] = m;
-            q[atomicAdd(qn, 1u)] = row;
+            const unsigned slot = atomicAdd(qn, 1u);
+            if (slot < kPmQueue)
+                q[slot] = row;
+            else
+                next[atomicAdd(&ctr->next_size, 1u)] = row;
         }
     }
 };
@@ -88,18 +102,18 @@ __global__ void __launch_bounds__(kPmThreads) pull_min_kernel(
     const uint32_t* __restrict__ tile_row, uint32_t* __restrict__ tile_head, uint32_t* __restrict__ tile_tail,
     uint64_t tiles, uint32_t n, uint64_t m, uint32_t* __restrict__ next, PushCounters* __restrict__ ctr) {
     __shared__ MpShared<kPmThreads, kPmItems, uint32_t> sh;
-    __shared__ uint32_t s_q[kMpTile];
+    __shared__ uint32_t s_q[kPmQueue];
     __shared__ unsigned int s_qn, s_recv, s_base;
     if (threadIdx.x == 0) {
         s_qn = 0;
         s_recv = 0;
     }
     PmGather<kAddWeight, kWeightKind> gather{csc_src, csc_w8, csc_w32, sval, &ctr->status};
-    PmEmit<kRecv> emit{val, s_q, &s_qn, &s_recv};
+    PmEmit<kRecv> emit{val, s_q, &s_qn, &s_recv, next, ctr};
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         mp_tile<kPmThreads, kPmItems, MinU32>(sh, csc_off, n, m, tile_row, tile, tile_head, tile_tail, gather, emit);
         __syncthreads();
-        const unsigned qn = s_qn;
+        const unsigned qn = min(s_qn, kPmQueue);
         if (qn) {
             if (threadIdx.x == 0) s_base = atomicAdd(&ctr->next_size, qn);
             __syncthreads();
@@ -136,32 +150,22 @@ __global__ void pull_min_fixup_kernel(const uint64_t* __restrict__ csc_off, cons
     }
 }
 
-unsigned pm_grid(ipg_graph* g) {
-    static int per_sm = 0;
-    if (!per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pull_min_kernel<true, 1, false>, kPmThreads, 0) !=
-                cudaSuccess ||
-            per_sm < 1)
-            per_sm = 1;
-    }
-    uint64_t grid = (uint64_t)sm_count_of(g->device) * per_sm;
-    if (grid > g->pr_tiles) grid = g->pr_tiles;
-    return (unsigned)(grid ? grid : 1);
-}
-
 template <bool kAddWeight, int kWeightKind, bool kRecv>
-void launch(ipg_graph* g, uint32_t* val, uint32_t* next, cudaStream_t st) {
-    pull_min_kernel<kAddWeight, kWeightKind, kRecv><<<pm_grid(g), kPmThreads, 0, st>>>(
+ipg_status launch(ipg_graph* g, uint32_t* val, uint32_t* next, cudaStream_t st) {
+    const void* k = reinterpret_cast<const void*>(&pull_min_kernel<kAddWeight, kWeightKind, kRecv>);
+    unsigned grid = 1;
+    IPG_TRY(pull_grid(&k, 1, kPmThreads, g->device, g->pr_tiles, (int)tuning().pr_carveout, &grid));
+    pull_min_kernel<kAddWeight, kWeightKind, kRecv><<<grid, kPmThreads, 0, st>>>(
         g->csc_off, g->csc_src, g->csc_w8, g->csc_w, g->sval, val, g->pr_tile_row, (uint32_t*)g->pr_head,
         (uint32_t*)g->pr_tail, g->pr_tiles, g->n, g->m, next, g->counters);
+    IPG_CUDA(cudaGetLastError());
+    return IPG_OK;
 }
 
 template <bool kAddWeight, int kWeightKind>
-void launch2(bool recv, ipg_graph* g, uint32_t* val, uint32_t* next, cudaStream_t st) {
-    if (recv)
-        launch<kAddWeight, kWeightKind, true>(g, val, next, st);
-    else
-        launch<kAddWeight, kWeightKind, false>(g, val, next, st);
+ipg_status launch2(bool recv, ipg_graph* g, uint32_t* val, uint32_t* next, cudaStream_t st) {
+    return recv ? launch<kAddWeight, kWeightKind, true>(g, val, next, st)
+                : launch<kAddWeight, kWeightKind, false>(g, val, next, st);
 }
 
 unsigned small_grid(uint64_t work) {
@@ -188,14 +192,13 @@ ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, const uint32_t
     IPG_CUDA(cudaGetLastError());
     if (ev_kernel) IPG_CUDA(cudaEventRecord(ev_kernel, st));
     if (!sssp)
-        launch2<false, 0>(recv, g, val, next, st);
+        IPG_TRY((launch2<false, 0>(recv, g, val, next, st)));
     else if (g->csc_w8)
-        launch2<true, 1>(recv, g, val, next, st);
+        IPG_TRY((launch2<true, 1>(recv, g, val, next, st)));
     else if (g->csc_w)
-        launch2<true, 2>(recv, g, val, next, st);
+        IPG_TRY((launch2<true, 2>(recv, g, val, next, st)));
     else
-        launch2<true, 0>(recv, g, val, next, st);
-    IPG_CUDA(cudaGetLastError());
+        IPG_TRY((launch2<true, 0>(recv, g, val, next, st)));
     if (recv)
         pull_min_fixup_kernel<true><<<small_grid(g->pr_tiles), 256, 0, st>>>(
             g->csc_off, g->pr_tile_row, (const uint32_t*)g->pr_head, (const uint32_t*)g->pr_tail, val, g->pr_tiles,
