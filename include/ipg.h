@@ -368,11 +368,65 @@ void ipg_server_destroy(ipg_server* s);
  *   "combine_warp"  ipg_sssp_tree / ipg_bfs_paths: 1 = lanes of a warp that send to
  *                   the same vertex fold their messages first (IPG_COMBINE_WARP),
  *                   0 = every message goes to the mailbox.  Default 0.
+ *   "pr_engine"     PageRank pull kernel: 0 = messages staged in shared memory,
+ *                   1 = messages loaded into registers, row ends as a bit mask.
+ *                   Both add in the same order: ranks are bit-identical.  Default 0.
+ *   "pr_threads"    PageRank pull kernel: 256 or 512 threads per merge-path tile.
+ *                   The per-thread summation runs change with it, so ranks may
+ *                   differ in the last bits (both stay within the float tolerance).
+ *                   Default 256.
+ *   "pr_carveout"   pull kernels: shared-memory carveout in percent of the SM's
+ *                   unified L1/shared array; -1 = the smallest that keeps the
+ *                   kernel's full occupancy, leaving the rest to L1, which caches
+ *                   the messages of the most-connected senders.  Default -1.
  * Unknown names or invalid values return IPG_EINVAL.  Set knobs between calls,
- * not while a call runs.
+ * not while a call runs.  A graph tuned by ipg_autotune uses its own values of
+ * pull_divisor, pr_engine and pr_carveout instead of these.
  */
 ipg_status ipg_set_tuning(const char* name, int64_t value);
 ipg_status ipg_get_tuning(const char* name, int64_t* value);
+
+/*
+ * ipg_autotune — pick the launch shape of the calls above for one graph by
+ * timing them on it (no counterpart in the paper: its OpenMP versions fix one
+ * schedule per benchmark, Sec. V-B and VI-C).
+ *   programs     IPG_TUNE_* bits: which programs to tune.  IPG_TUNE_HASHMIN
+ *                needs an undirected graph (IPG_EINVAL otherwise).
+ *   sssp_source  caller id of the SSSP source to time with; >= n picks the
+ *                vertex of largest total degree.
+ *   report       optional, out: the chosen values and the timings.
+ *   stream       cudaStream_t as void* for the timed runs.
+ * Candidates, all of which give bit-identical results (min combiners are
+ * order-free; both PageRank engines and every carveout add in one order):
+ *   Hashmin, SSSP  pull_divisor in {0, 2, 4, 6, 10, 16, 32};
+ *   PageRank       (pr_engine, pr_carveout) in {(0,-1), (0,60), (1,-1), (1,5)}.
+ * Each candidate runs twice (the faster run counts): Hashmin and SSSP to
+ * quiescence, PageRank for 3 updates, into a scratch buffer of n words that the
+ * call allocates and frees.  The winners are stored in the graph and used by
+ * every later call on it.  Results are cached per graph and in a process-wide
+ * table keyed by the graph's shape (n, m, directedness, weights, the largest
+ * out-degree and 64 sampled offsets), so tuning an identical graph again costs
+ * nothing; IPG_TUNE_FORCE re-times.  Errors: IPG_EINVAL (NULL graph, unknown
+ * bits, Hashmin on a directed graph), IPG_ECUDA/IPG_ENOMEM; the graph then keeps
+ * its previous tuning.
+ */
+#define IPG_TUNE_PAGERANK 1u
+#define IPG_TUNE_HASHMIN 2u
+#define IPG_TUNE_SSSP 4u
+#define IPG_TUNE_FORCE 0x100u
+
+typedef struct {
+    uint32_t programs;          /* programs the graph is tuned for after the call */
+    uint32_t cached;            /* 1: every requested program came from a cache */
+    int64_t hashmin_pull_divisor, sssp_pull_divisor, pr_engine, pr_carveout;  /* -1 = not tuned */
+    float hashmin_ms, sssp_ms, pagerank_ms;                 /* best candidate's run, 0 if not timed */
+    float hashmin_default_ms, sssp_default_ms, pagerank_default_ms;  /* the process-wide knobs' run */
+    uint32_t candidates_timed;  /* runs made by this call */
+    uint32_t reserved;
+} ipg_tune_report;
+
+ipg_status ipg_autotune(ipg_graph* g, uint32_t programs, uint32_t sssp_source, ipg_tune_report* report,
+                        void* stream);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char* ipg_last_error(void);

@@ -472,6 +472,13 @@ Tuning& tuning() {
     return t;
 }
 
+long long pull_divisor_for(const ipg_graph* g, bool sssp) {
+    if (sssp ? g->tuned.sssp : g->tuned.cc) return sssp ? g->tuned.sssp_divisor : g->tuned.cc_divisor;
+    return tuning().pull_divisor;
+}
+long long pr_engine_for(const ipg_graph* g) { return g->tuned.pr ? g->tuned.pr_engine : tuning().pr_engine; }
+long long pr_carveout_for(const ipg_graph* g) { return g->tuned.pr ? g->tuned.pr_carveout : tuning().pr_carveout; }
+
 // ---------------------------------------------------------------------------
 // creation
 

@@ -63,6 +63,13 @@ struct DeviceGuard {
     }
 };
 
+// knobs an autotuned graph carries instead of the process-wide ones
+struct GraphTuning {
+    bool pr = false, cc = false, sssp = false;
+    long long pr_engine = 0, pr_carveout = -1;
+    long long cc_divisor = 6, sssp_divisor = 6;
+};
+
 // per-superstep CUDA events (IPG_STAT_TIMING)
 struct StepTimer {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -140,6 +147,7 @@ struct ipg_graph {
 
     cudaStream_t stream = nullptr;  // used by the host-buffer entry points
     ipg::StepTimer timer;
+    ipg::GraphTuning tuned;         // set by ipg_autotune
 };
 
 namespace ipg {
@@ -178,6 +186,10 @@ struct Tuning {
     long long pr_engine = 0;     // PageRank pull kernel: 0 staged messages, 1 direct (registers)
 };
 Tuning& tuning();
+// the graph's tuned value where it has one, else the process-wide knob
+long long pull_divisor_for(const ipg_graph* g, bool sssp);
+long long pr_engine_for(const ipg_graph* g);
+long long pr_carveout_for(const ipg_graph* g);
 // stats helpers
 void stats_begin(ipg_stats* s);
 void stats_put(ipg_stats* s, uint32_t idx, const ipg_superstep_stats& rec);

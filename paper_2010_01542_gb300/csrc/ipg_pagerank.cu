@@ -235,9 +235,9 @@ static const void* pr_kernel_for(int threads, bool direct) {
 ipg_status pr_launch_shape(ipg_graph* g, PrLaunch* L) {
     const Tuning& tu = tuning();
     L->threads = tu.pr_threads == 512 ? 512 : 256;
-    L->direct = tu.pr_engine == 1;
+    L->direct = pr_engine_for(g) == 1;
     const void* k[2] = {pr_kernel_for<false>(L->threads, L->direct), pr_kernel_for<true>(L->threads, L->direct)};
-    return pull_grid(k, 2, L->threads, g->device, g->pr_tiles, (int)tu.pr_carveout, &L->grid);
+    return pull_grid(k, 2, L->threads, g->device, g->pr_tiles, (int)pr_carveout_for(g), &L->grid);
 }
 
 template <bool kFinal, int kThreads, bool kDirect>

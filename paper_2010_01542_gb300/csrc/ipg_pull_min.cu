@@ -154,7 +154,7 @@ template <bool kAddWeight, int kWeightKind, bool kRecv>
 ipg_status launch(ipg_graph* g, uint32_t* val, uint32_t* next, cudaStream_t st) {
     const void* k = reinterpret_cast<const void*>(&pull_min_kernel<kAddWeight, kWeightKind, kRecv>);
     unsigned grid = 1;
-    IPG_TRY(pull_grid(&k, 1, kPmThreads, g->device, g->pr_tiles, (int)tuning().pr_carveout, &grid));
+    IPG_TRY(pull_grid(&k, 1, kPmThreads, g->device, g->pr_tiles, (int)pr_carveout_for(g), &grid));
     pull_min_kernel<kAddWeight, kWeightKind, kRecv><<<grid, kPmThreads, 0, st>>>(
         g->csc_off, g->csc_src, g->csc_w8, g->csc_w, g->sval, val, g->pr_tile_row, (uint32_t*)g->pr_head,
         (uint32_t*)g->pr_tail, g->pr_tiles, g->n, g->m, next, g->counters);

@@ -494,7 +494,7 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
         }
         // direction: a superstep whose messages reach m / pull_divisor runs in pull form
         bool pull = false;
-        const long long div = tuning().pull_divisor;
+        const long long div = pull_divisor_for(g, kind == kSssp);
         // a frontier of f vertices sends at most f * max_outdeg messages: read the exact
         // count back (one more host sync) only when that bound reaches m / pull_divisor
         if (div > 0 && g->m && (double)f * (double)g->max_outdeg * (double)div >= (double)g->m) {
