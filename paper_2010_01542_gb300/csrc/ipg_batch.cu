@@ -20,6 +20,15 @@
 // Senders therefore send the value they had at the start of the superstep, as in
 // the synchronous model, and every source's distances and superstep count equal
 // those of a standalone ipg_sssp run.
+//
+// The superstep loop runs on the device: a CUDA graph holds a conditional WHILE
+// node whose body is one superstep (pull, reset, apply, step).  The kernels read
+// the frontier from a device control block, so their launch parameters never
+// change, and the step kernel decides whether another superstep follows.  One
+// graph launch runs at most kLoopCap supersteps; the host reads the control
+// block after each launch and relaunches while supersteps remain, so a group
+// costs a few host synchronisations instead of two per superstep, and no launch
+// can loop without bound.
 #include "ipg_internal.cuh"
 
 namespace ipg {
@@ -29,12 +38,31 @@ constexpr int kLanes = 32;
 constexpr uint32_t kChunk = 256;  // in-edges per warp task
 constexpr int kUnroll = 4;         // sender lines in flight per warp
 
+constexpr unsigned kLoopCap = 64;  // supersteps per graph launch
+
 struct BatchCounters {
     unsigned long long msgs[kLanes];  // messages the next superstep's senders send, per source
     unsigned int next_size;
     unsigned int status;
     unsigned int pad[14];
 };
+
+// device-resident loop state of one group
+struct BatchCtl {
+    unsigned int cur;     // frontier buffer holding the current senders
+    unsigned int f;       // current senders
+    unsigned int iter;    // supersteps run by the current graph launch
+    unsigned int done;    // 1: no superstep left
+    unsigned int status;  // kStatus* bits
+    unsigned int count[kLanes];  // supersteps of each source's Pregel run
+};
+
+__device__ __forceinline__ uint32_t* fr_cur(uint32_t* fr0, uint32_t* fr1, const BatchCtl* ctl) {
+    return ctl->cur ? fr1 : fr0;
+}
+__device__ __forceinline__ uint32_t* fr_next(uint32_t* fr0, uint32_t* fr1, const BatchCtl* ctl) {
+    return ctl->cur ? fr0 : fr1;
+}
 
 __global__ void chunk_rows_kernel(const uint64_t* __restrict__ off, uint32_t n, uint64_t m, uint64_t chunks,
                                   uint32_t* __restrict__ chunk_row) {
@@ -91,7 +119,9 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
     const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ csc_src, const uint8_t* __restrict__ w8,
     const uint32_t* __restrict__ w32, const uint32_t* __restrict__ chunk_row, uint64_t chunks, uint32_t n, uint64_t m,
     const uint32_t* __restrict__ sval, const uint32_t* __restrict__ smask, uint32_t* __restrict__ dist,
-    uint32_t* __restrict__ cmask, uint32_t* __restrict__ next, BatchCounters* __restrict__ ctr) {
+    uint32_t* __restrict__ cmask, uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl,
+    BatchCounters* __restrict__ ctr) {
+    uint32_t* __restrict__ next = fr_next(fr0, fr1, ctl);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -184,8 +214,10 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
 }
 
 // previous senders: snapshot rows back to kInf
-__global__ void batch_reset_kernel(const uint32_t* __restrict__ F, uint32_t f, uint32_t* __restrict__ sval,
-                                   uint32_t* __restrict__ smask) {
+__global__ void batch_reset_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl,
+                                   uint32_t* __restrict__ sval, uint32_t* __restrict__ smask) {
+    const uint32_t* __restrict__ F = fr_cur(fr0, fr1, ctl);
+    const uint32_t f = ctl->f;
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -197,10 +229,12 @@ __global__ void batch_reset_kernel(const uint32_t* __restrict__ F, uint32_t f, u
 }
 
 // next senders: publish their new values, count their messages per source
-__global__ void batch_apply_kernel(const uint32_t* __restrict__ F, uint32_t f, const uint64_t* __restrict__ off,
-                                   const uint32_t* __restrict__ dist, uint32_t* __restrict__ sval,
-                                   uint32_t* __restrict__ smask, uint32_t* __restrict__ cmask,
-                                   BatchCounters* __restrict__ ctr) {
+__global__ void batch_apply_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl, uint32_t n,
+                                   const uint64_t* __restrict__ off, const uint32_t* __restrict__ dist,
+                                   uint32_t* __restrict__ sval, uint32_t* __restrict__ smask,
+                                   uint32_t* __restrict__ cmask, BatchCounters* __restrict__ ctr) {
+    const uint32_t* __restrict__ F = fr_next(fr0, fr1, ctl);
+    const uint32_t f = min(ctr->next_size, n);  // a larger count is reported by the step kernel
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -218,6 +252,55 @@ __global__ void batch_apply_kernel(const uint32_t* __restrict__ F, uint32_t f, c
         }
     }
     if (msgs) atomicAdd(&ctr->msgs[lane], msgs);
+}
+
+// the group's loop state after the seed: superstep 0 counts for every source,
+// superstep 1 for those whose source has out-edges
+__global__ void batch_init_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t k) {
+    const uint32_t b = threadIdx.x;
+    if (b < kLanes) {
+        ctl->count[b] = b < k ? 1u + (ctr->msgs[b] > 0 ? 1u : 0u) : 0u;
+        ctr->msgs[b] = 0;
+    }
+    __syncwarp();
+    if (b == 0) {
+        ctl->cur = 0;
+        ctl->f = ctr->next_size;
+        ctl->iter = 0;
+        ctl->done = ctr->next_size == 0;
+        ctl->status = 0;
+        ctr->next_size = 0;
+        ctr->status = 0;
+    }
+}
+
+// End of a superstep: per-source counts, the next frontier becomes current, the
+// counters are cleared for the next superstep, and the WHILE condition says
+// whether the graph runs another one (not past kLoopCap in one launch).
+__global__ void batch_step_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t n,
+                                  cudaGraphConditionalHandle loop) {
+    const uint32_t b = threadIdx.x;
+    if (b < kLanes) {
+        if (ctr->msgs[b] > 0) ++ctl->count[b];
+        ctr->msgs[b] = 0;
+    }
+    __syncwarp();
+    if (b == 0) {
+        const uint32_t fn = ctr->next_size;
+        uint32_t status = ctl->status | ctr->status;
+        if (fn > n) status |= kStatusInternal;
+        ctl->status = status;
+        ctl->f = fn <= n ? fn : 0u;
+        ctl->cur ^= 1u;
+        ctr->next_size = 0;
+        ctr->status = 0;
+        const bool more = ctl->f > 0 && status == 0;
+        ctl->done = !more;
+        const unsigned it = ctl->iter + 1;
+        const bool again = more && it < kLoopCap;
+        ctl->iter = again ? it : 0u;
+        cudaGraphSetConditional(loop, again ? 1u : 0u);
+    }
 }
 
 // out[b][v] = dist[inv[v]][b] for b < k, through a shared-memory transpose
@@ -255,7 +338,9 @@ struct BatchWorkspace {
     uint64_t chunks = 0;
     uint32_t* src_int = nullptr;  // [32]
     BatchCounters* ctr = nullptr;
-    BatchCounters* h_ctr = nullptr;
+    BatchCtl* ctl = nullptr;
+    BatchCtl* h_ctl = nullptr;  // pinned mirror
+    cudaGraphExec_t loop[3] = {nullptr, nullptr, nullptr};  // superstep loop, per weight kind
 };
 
 void batch_free(ipg_graph* g) {
@@ -270,7 +355,10 @@ void batch_free(ipg_graph* g) {
     cudaFree(b->chunk_row);
     cudaFree(b->src_int);
     cudaFree(b->ctr);
-    if (b->h_ctr) cudaFreeHost(b->h_ctr);
+    cudaFree(b->ctl);
+    if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    for (int i = 0; i < 3; ++i)
+        if (b->loop[i]) cudaGraphExecDestroy(b->loop[i]);
     delete b;
     g->batch = nullptr;
 }
@@ -289,7 +377,8 @@ static ipg_status batch_prepare(ipg_graph* g, cudaStream_t st) {
     IPG_CUDA(cudaMalloc(&b->fr[1], sizeof(uint32_t) * (size_t)n));
     IPG_CUDA(cudaMalloc(&b->src_int, sizeof(uint32_t) * kLanes));
     IPG_CUDA(cudaMalloc(&b->ctr, sizeof(BatchCounters)));
-    IPG_CUDA(cudaHostAlloc(&b->h_ctr, sizeof(BatchCounters), cudaHostAllocDefault));
+    IPG_CUDA(cudaMalloc(&b->ctl, sizeof(BatchCtl)));
+    IPG_CUDA(cudaHostAlloc(&b->h_ctl, sizeof(BatchCtl), cudaHostAllocDefault));
     b->chunks = (g->m + kChunk - 1) / kChunk;
     IPG_CUDA(cudaMalloc(&b->chunk_row, sizeof(uint32_t) * (b->chunks ? b->chunks : 1)));
     if (b->chunks) {
@@ -300,12 +389,73 @@ static ipg_status batch_prepare(ipg_graph* g, cudaStream_t st) {
     return IPG_OK;
 }
 
+// the superstep body, enqueued on `st` (captured into the loop graph)
+static void batch_superstep(ipg_graph* g, BatchWorkspace* b, int wkind, cudaGraphConditionalHandle loop,
+                            cudaStream_t st) {
+    const int sms = sm_count_of(g->device);
+    const unsigned grid = grid_for_warps(b->chunks, sms);
+    const unsigned fixed = (unsigned)sms * 8;  // frontier passes: persistent, the size is read on the device
+#define IPG_BATCH_PULL(K)                                                                                         \
+    batch_pull_kernel<K><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,       \
+                                               b->chunks, g->n, g->m, b->sval, b->smask, b->dist, b->cmask,      \
+                                               b->fr[0], b->fr[1], b->ctl, b->ctr)
+    if (wkind == 1)
+        IPG_BATCH_PULL(1);
+    else if (wkind == 2)
+        IPG_BATCH_PULL(2);
+    else
+        IPG_BATCH_PULL(0);
+#undef IPG_BATCH_PULL
+    batch_reset_kernel<<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, b->sval, b->smask);
+    batch_apply_kernel<<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, g->n, g->off, b->dist, b->sval, b->smask,
+                                              b->cmask, b->ctr);
+    batch_step_kernel<<<1, kLanes, 0, st>>>(b->ctl, b->ctr, g->n, loop);
+}
+
+// Builds the graph [WHILE (cond) { superstep }] for this workspace and weight kind.
+static ipg_status batch_loop_graph(ipg_graph* g, BatchWorkspace* b, int wkind) {
+    if (b->loop[wkind]) return IPG_OK;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap = nullptr;
+    ipg_status rc = IPG_OK;
+    do {
+        cudaError_t e = cudaGraphCreate(&graph, 0);
+        cudaGraphConditionalHandle handle;
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = handle;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(cap, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "batch loop graph", __FILE__, __LINE__);
+            break;
+        }
+        batch_superstep(g, b, wkind, handle, cap);
+        cudaGraph_t body = nullptr;
+        e = cudaStreamEndCapture(cap, &body);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->loop[wkind], graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch loop graph capture", __FILE__, __LINE__);
+    } while (false);
+    if (cap) cudaStreamDestroy(cap);
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+}
+
 // one group of k <= 32 sources (caller ids) -> out rows [0, k), row stride out_stride
 static ipg_status batch_group(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* out, uint64_t out_stride,
                               uint32_t* supersteps, cudaStream_t st) {
     BatchWorkspace* b = (BatchWorkspace*)g->batch;
     const uint32_t n = g->n;
     const int sms = sm_count_of(g->device);
+    const int wkind = g->csc_w8 ? 1 : g->csc_w ? 2 : 0;
+    IPG_TRY(batch_loop_graph(g, b, wkind));
     // caller ids -> internal ids (inv is device-resident)
     uint32_t h_src[kLanes];
     for (uint32_t i = 0; i < k; ++i) h_src[i] = sources[i];
@@ -318,52 +468,26 @@ static ipg_status batch_group(ipg_graph* g, const uint32_t* sources, uint32_t k,
     IPG_TRY(map_to_internal(g, b->src_int, k, st));
     batch_seed_kernel<<<1, kLanes, 0, st>>>(b->src_int, k, g->off, b->dist, b->sval, b->smask, b->fr[0], b->ctr);
     IPG_CUDA(cudaGetLastError());
-    IPG_CUDA(cudaMemcpyAsync(b->h_ctr, b->ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, st));
+    batch_init_kernel<<<1, kLanes, 0, st>>>(b->ctl, b->ctr, k);
+    IPG_CUDA(cudaGetLastError());
+    IPG_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
     IPG_CUDA(cudaStreamSynchronize(st));
-    uint32_t count[kLanes];
-    for (uint32_t i = 0; i < k; ++i) count[i] = 1 + (b->h_ctr->msgs[i] > 0 ? 1 : 0);
-    uint32_t f = b->h_ctr->next_size;
-    int cur = 0;
-    for (uint32_t s = 0; f > 0; ++s) {
-        IPG_CUDA(cudaMemsetAsync(b->ctr, 0, sizeof(BatchCounters), st));
-        const unsigned grid = grid_for_warps(b->chunks, sms);
-        if (g->csc_w8)
-            batch_pull_kernel<1><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,
-                                                       b->chunks, n, g->m, b->sval, b->smask, b->dist, b->cmask,
-                                                       b->fr[cur ^ 1], b->ctr);
-        else if (g->csc_w)
-            batch_pull_kernel<2><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,
-                                                       b->chunks, n, g->m, b->sval, b->smask, b->dist, b->cmask,
-                                                       b->fr[cur ^ 1], b->ctr);
-        else
-            batch_pull_kernel<0><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,
-                                                       b->chunks, n, g->m, b->sval, b->smask, b->dist, b->cmask,
-                                                       b->fr[cur ^ 1], b->ctr);
-        IPG_CUDA(cudaGetLastError());
-        batch_reset_kernel<<<grid_for_warps(f, sms), 256, 0, st>>>(b->fr[cur], f, b->sval, b->smask);
-        IPG_CUDA(cudaGetLastError());
-        IPG_CUDA(cudaMemcpyAsync(&b->h_ctr->next_size, &b->ctr->next_size, sizeof(unsigned),
-                                 cudaMemcpyDeviceToHost, st));
+    // each launch runs supersteps on the device until the frontier is empty or kLoopCap
+    for (uint64_t launches = 0; !b->h_ctl->done; ++launches) {
+        if (launches > (uint64_t)n / kLoopCap + 2)
+            return set_error(IPG_EDEVICE, "ipg_sssp_batch: the superstep loop did not end after n supersteps");
+        IPG_CUDA(cudaGraphLaunch(b->loop[wkind], st));
+        IPG_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
         IPG_CUDA(cudaStreamSynchronize(st));
-        const uint32_t fn = b->h_ctr->next_size;
-        if (fn > n) return set_error(IPG_EDEVICE, "ipg_sssp_batch: frontier overflow");
-        if (fn) {
-            batch_apply_kernel<<<grid_for_warps(fn, sms), 256, 0, st>>>(b->fr[cur ^ 1], fn, g->off, b->dist, b->sval,
-                                                                      b->smask, b->cmask, b->ctr);
-            IPG_CUDA(cudaGetLastError());
-        }
-        IPG_CUDA(cudaMemcpyAsync(b->h_ctr, b->ctr, sizeof(BatchCounters), cudaMemcpyDeviceToHost, st));
-        IPG_CUDA(cudaStreamSynchronize(st));
-        if (b->h_ctr->status & kStatusOverflow) return set_error(IPG_EOVERFLOW, "ipg_sssp_batch: a path length reached UINT32_MAX");
-        for (uint32_t i = 0; i < k; ++i) count[i] += b->h_ctr->msgs[i] > 0 ? 1 : 0;
-        f = fn;
-        cur ^= 1;
+        if (b->h_ctl->status & kStatusOverflow)
+            return set_error(IPG_EOVERFLOW, "ipg_sssp_batch: a path length reached UINT32_MAX");
+        if (b->h_ctl->status & kStatusInternal) return set_error(IPG_EDEVICE, "ipg_sssp_batch: frontier overflow");
     }
     batch_output_kernel<<<grid_for_warps((uint64_t)n, sms), 1024, 0, st>>>(b->dist, g->inv, n, k, out, out_stride);
     IPG_CUDA(cudaGetLastError());
     IPG_CUDA(cudaStreamSynchronize(st));
     if (supersteps)
-        for (uint32_t i = 0; i < k; ++i) supersteps[i] = count[i];
+        for (uint32_t i = 0; i < k; ++i) supersteps[i] = b->h_ctl->count[i];
     return IPG_OK;
 }
 

@@ -160,3 +160,17 @@ def test_hashmin_batch_device_and_errors(ipg):
     ref = oracle.hashmin(g.n, g.offsets, g.cols)
     np.testing.assert_array_equal(lab, ref.values)
     assert list(st) == [ref.supersteps]
+
+
+def test_batch_long_paths_span_several_graph_launches(ipg):
+    """A directed path of 300 vertices (plus a back edge and shortcuts) needs about
+    300 supersteps from vertex 0: the device-side loop stops every 64 supersteps and
+    the host relaunches it; counts and distances must still equal ipg_sssp's."""
+    n = 300
+    src = list(range(n - 1)) + [n - 1, 10, 100]
+    dst = list(range(1, n)) + [0, 200, 250]
+    w = np.array([1 + (i * 7) % 255 for i in range(len(src))], dtype=np.uint32)
+    g = gen.csr_from_edges(n, np.array(src), np.array(dst), weights=w)
+    sources = np.array([0, 1, 5, 150, 299, 0])
+    dist, steps = _check_batch(ipg, g, sources, g.weights, use_oracle=True)
+    assert steps.max() > 3 * 64
