@@ -379,9 +379,13 @@ void ipg_server_destroy(ipg_server* s);
  *                   unified L1/shared array; -1 = the smallest that keeps the
  *                   kernel's full occupancy, leaving the rest to L1, which caches
  *                   the messages of the most-connected senders.  Default -1.
+ *   "batch_divisor" ipg_sssp_batch: a superstep whose senders (union over the
+ *                   sources of a group) have fewer than m / batch_divisor out-edges
+ *                   runs in push form, else in pull form.  0 = always pull.
+ *                   Default 6.
  * Unknown names or invalid values return IPG_EINVAL.  Set knobs between calls,
  * not while a call runs.  A graph tuned by ipg_autotune uses its own values of
- * pull_divisor, pr_engine and pr_carveout instead of these.
+ * pull_divisor, batch_divisor, pr_engine and pr_carveout instead of these.
  */
 ipg_status ipg_set_tuning(const char* name, int64_t value);
 ipg_status ipg_get_tuning(const char* name, int64_t* value);
@@ -399,10 +403,13 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value);
  * Candidates, all of which give bit-identical results (min combiners are
  * order-free; both PageRank engines and every carveout add in one order):
  *   Hashmin, SSSP  pull_divisor in {0, 2, 4, 6, 10, 16, 32};
+ *   batched SSSP   batch_divisor in {0, 2, 4, 6, 10, 16, 32};
  *   PageRank       (pr_engine, pr_carveout) in {(0,-1), (0,60), (1,-1), (1,5)}.
  * Each candidate runs twice (the faster run counts): Hashmin and SSSP to
- * quiescence, PageRank for 3 updates, into a scratch buffer of n words that the
- * call allocates and frees.  The winners are stored in the graph and used by
+ * quiescence, batched SSSP on 32 sources (sssp_source and 31 caller ids spread
+ * evenly over [0, n)), PageRank for 3 updates, into a scratch buffer (32 n
+ * words with IPG_TUNE_SSSP_BATCH, else n) that the call allocates and frees.
+ * The winners are stored in the graph and used by
  * every later call on it.  Results are cached per graph and in a process-wide
  * table keyed by the graph's shape (n, m, directedness, weights, the largest
  * out-degree and 64 sampled offsets), so tuning an identical graph again costs
@@ -413,14 +420,15 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value);
 #define IPG_TUNE_PAGERANK 1u
 #define IPG_TUNE_HASHMIN 2u
 #define IPG_TUNE_SSSP 4u
+#define IPG_TUNE_SSSP_BATCH 8u
 #define IPG_TUNE_FORCE 0x100u
 
 typedef struct {
     uint32_t programs;          /* programs the graph is tuned for after the call */
     uint32_t cached;            /* 1: every requested program came from a cache */
-    int64_t hashmin_pull_divisor, sssp_pull_divisor, pr_engine, pr_carveout;  /* -1 = not tuned */
-    float hashmin_ms, sssp_ms, pagerank_ms;                 /* best candidate's run, 0 if not timed */
-    float hashmin_default_ms, sssp_default_ms, pagerank_default_ms;  /* the process-wide knobs' run */
+    int64_t hashmin_pull_divisor, sssp_pull_divisor, sssp_batch_divisor, pr_engine, pr_carveout;  /* -1 = not tuned */
+    float hashmin_ms, sssp_ms, sssp_batch_ms, pagerank_ms;  /* best candidate's run, 0 if not timed */
+    float hashmin_default_ms, sssp_default_ms, sssp_batch_default_ms, pagerank_default_ms;  /* process-wide knobs */
     uint32_t candidates_timed;  /* runs made by this call */
     uint32_t reserved;
 } ipg_tune_report;

@@ -330,15 +330,17 @@ __all__ += ["ipg_set_tuning", "ipg_get_tuning"]
 IPG_TUNE_PAGERANK = 1
 IPG_TUNE_HASHMIN = 2
 IPG_TUNE_SSSP = 4
+IPG_TUNE_SSSP_BATCH = 8
 IPG_TUNE_FORCE = 0x100
 
 
 class _CTuneReport(ctypes.Structure):
     _fields_ = [("programs", ctypes.c_uint32), ("cached", ctypes.c_uint32),
                 ("hashmin_pull_divisor", ctypes.c_int64), ("sssp_pull_divisor", ctypes.c_int64),
-                ("pr_engine", ctypes.c_int64), ("pr_carveout", ctypes.c_int64),
-                ("hashmin_ms", ctypes.c_float), ("sssp_ms", ctypes.c_float), ("pagerank_ms", ctypes.c_float),
-                ("hashmin_default_ms", ctypes.c_float), ("sssp_default_ms", ctypes.c_float),
+                ("sssp_batch_divisor", ctypes.c_int64), ("pr_engine", ctypes.c_int64), ("pr_carveout", ctypes.c_int64),
+                ("hashmin_ms", ctypes.c_float), ("sssp_ms", ctypes.c_float), ("sssp_batch_ms", ctypes.c_float),
+                ("pagerank_ms", ctypes.c_float), ("hashmin_default_ms", ctypes.c_float),
+                ("sssp_default_ms", ctypes.c_float), ("sssp_batch_default_ms", ctypes.c_float),
                 ("pagerank_default_ms", ctypes.c_float), ("candidates_timed", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
 
@@ -354,7 +356,8 @@ def ipg_autotune(g: Graph, programs: int, sssp_source: int = INF, stream=None) -
     return {name: getattr(rep, name) for name, _ in _CTuneReport._fields_ if name != "reserved"}
 
 
-__all__ += ["ipg_autotune", "IPG_TUNE_PAGERANK", "IPG_TUNE_HASHMIN", "IPG_TUNE_SSSP", "IPG_TUNE_FORCE"]
+__all__ += ["ipg_autotune", "IPG_TUNE_PAGERANK", "IPG_TUNE_HASHMIN", "IPG_TUNE_SSSP", "IPG_TUNE_SSSP_BATCH",
+            "IPG_TUNE_FORCE"]
 
 
 def _sources_arr(sources, n):

@@ -21,6 +21,13 @@
 // the synchronous model, and every source's distances and superstep count equal
 // those of a standalone ipg_sssp run.
 //
+// A sparse superstep runs in push form instead: a task pass cuts the senders'
+// out-edge lists into tasks of kPushChunk edges, and a warp per task sends
+// sval[u][b] + w along each out-edge (u -> v) with atomicMin into dist[v][b].
+// Push and pull take the minimum of the same messages and mark the same
+// lowered lanes, so they are interchangeable; the step kernel picks push when
+// the senders' out-edges (summed by the apply pass) are fewer than m / divisor.
+//
 // The superstep loop runs on the device: a CUDA graph holds a conditional WHILE
 // node whose body is one superstep (pull, reset, apply, step).  The kernels read
 // the frontier from a device control block, so their launch parameters never
@@ -38,13 +45,16 @@ constexpr int kLanes = 32;
 constexpr uint32_t kChunk = 256;  // in-edges per warp task
 constexpr int kUnroll = 4;         // sender lines in flight per warp
 
-constexpr unsigned kLoopCap = 64;  // supersteps per graph launch
+constexpr unsigned kLoopCap = 64;      // supersteps per graph launch
+constexpr uint32_t kPushChunk = 256;   // out-edges per push task
 
 struct BatchCounters {
     unsigned long long msgs[kLanes];  // messages the next superstep's senders send, per source
+    unsigned long long edges;         // out-edges of the next senders (union over sources)
     unsigned int next_size;
     unsigned int status;
-    unsigned int pad[14];
+    unsigned int ntasks;              // push tasks of the current senders (push supersteps)
+    unsigned int pad[11];
 };
 
 // device-resident loop state of one group
@@ -54,6 +64,8 @@ struct BatchCtl {
     unsigned int iter;    // supersteps run by the current graph launch
     unsigned int done;    // 1: no superstep left
     unsigned int status;  // kStatus* bits
+    unsigned int push;    // 1: the current superstep runs in push form
+    unsigned long long divisor;  // push when the senders' out-edges * divisor < m (0: always pull)
     unsigned int count[kLanes];  // supersteps of each source's Pregel run
 };
 
@@ -94,8 +106,12 @@ __global__ void batch_seed_kernel(const uint32_t* __restrict__ src_int, uint32_t
         dist[(uint64_t)v * kLanes + b] = 0;
         sval[(uint64_t)v * kLanes + b] = 0;
         const unsigned old = atomicOr(&smask[v], 1u << b);
-        if (old == 0) frontier[atomicAdd(&ctr->next_size, 1u)] = v;
-        ctr->msgs[b] = off[v + 1] - off[v];
+        const uint64_t deg = off[v + 1] - off[v];
+        if (old == 0) {
+            frontier[atomicAdd(&ctr->next_size, 1u)] = v;
+            atomicAdd(&ctr->edges, (unsigned long long)deg);
+        }
+        ctr->msgs[b] = deg;
     }
 }
 
@@ -121,6 +137,7 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
     const uint32_t* __restrict__ sval, const uint32_t* __restrict__ smask, uint32_t* __restrict__ dist,
     uint32_t* __restrict__ cmask, uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl,
     BatchCounters* __restrict__ ctr) {
+    if (ctl->push) return;
     uint32_t* __restrict__ next = fr_next(fr0, fr1, ctl);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -213,6 +230,120 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
     }
 }
 
+// Push supersteps only: the current senders' out-edge lists as tasks of
+// kPushChunk edges, (sender << 32 | chunk).  A warp takes 32 senders at a time
+// and claims their tasks with one atomic.
+__global__ void batch_tasks_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl,
+                                   const uint64_t* __restrict__ off, unsigned long long* __restrict__ tasks,
+                                   BatchCounters* __restrict__ ctr) {
+    if (!ctl->push) return;
+    const uint32_t* __restrict__ F = fr_cur(fr0, fr1, ctl);
+    const uint32_t f = ctl->f;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t i0 = warp * 32; i0 < f; i0 += nwarps * 32) {
+        const uint64_t i = i0 + lane;
+        uint32_t u = 0, nt = 0;
+        if (i < f) {
+            u = F[i];
+            nt = (uint32_t)((off[u + 1] - off[u] + kPushChunk - 1) / kPushChunk);
+        }
+        uint32_t incl = nt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += x;
+        }
+        unsigned base = 0;
+        if (lane == 31 && incl) base = atomicAdd(&ctr->ntasks, incl);
+        base = __shfl_sync(0xFFFFFFFFu, base, 31) + incl - nt;
+        for (uint32_t c = 0; c < nt; ++c) tasks[base + c] = ((unsigned long long)u << 32) | c;
+    }
+}
+
+// candidate s + w for a sender value s < kInf; a sum reaching kInf is reported
+__device__ __forceinline__ uint32_t batch_cand(uint32_t s, uint32_t w, BatchCounters* __restrict__ ctr) {
+    unsigned long long d = (unsigned long long)s + w;
+    if (d >= kInf) {
+        atomicOr(&ctr->status, kStatusOverflow);
+        d = kInf - 1;
+    }
+    return (uint32_t)d;
+}
+
+// Push form of a superstep: a warp per task (sender u, chunk of its out-edges).
+// When few sources send from u (kSparseLanes or fewer), lanes take different
+// edges and loop over those sources, one atomicMin per (edge, source); else
+// lane b sends sval[u][b] + w along each edge, one coalesced row per edge.
+constexpr int kSparseLanes = 4;
+
+template <int kWeightKind>
+__global__ void __launch_bounds__(256) batch_push_kernel(
+    const uint64_t* __restrict__ off, const uint32_t* __restrict__ col, const uint8_t* __restrict__ w8,
+    const uint32_t* __restrict__ w32, const unsigned long long* __restrict__ tasks,
+    const uint32_t* __restrict__ sval, const uint32_t* __restrict__ smask, uint32_t* __restrict__ dist,
+    uint32_t* __restrict__ cmask, uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl,
+    BatchCounters* __restrict__ ctr) {
+    if (!ctl->push) return;
+    uint32_t* __restrict__ next = fr_next(fr0, fr1, ctl);
+    const uint32_t nt = ctr->ntasks;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t t = warp; t < nt; t += nwarps) {
+        const unsigned long long task = tasks[t];
+        const uint32_t u = (uint32_t)(task >> 32);
+        const uint64_t e_beg = off[u] + (uint64_t)(uint32_t)task * kPushChunk;
+        const uint64_t e_end = min(off[u + 1], e_beg + kPushChunk);
+        const uint32_t senders = smask[u];  // sources that send from u (warp-uniform)
+        if (__popc(senders) <= kSparseLanes) {
+            // lane per edge (no warp-collective step); the sending sources one after another
+            for (uint64_t j = e_beg + lane; j < e_end; j += 32) {
+                const uint32_t v = __ldg(col + j);
+                uint32_t w = 1;
+                if (kWeightKind == 1) w = __ldg(w8 + j);
+                if (kWeightKind == 2) w = __ldg(w32 + j);
+                for (uint32_t rest = senders; rest; rest &= rest - 1) {
+                    const uint32_t b = __ffs(rest) - 1;
+                    const uint32_t s = __ldg(sval + (uint64_t)u * kLanes + b);
+                    if (s != kInf) {
+                        const uint32_t d = batch_cand(s, w, ctr);
+                        if (d < atomicMin(&dist[(uint64_t)v * kLanes + b], d)) {
+                            if (atomicOr(&cmask[v], 1u << b) == 0) next[atomicAdd(&ctr->next_size, 1u)] = v;
+                        }
+                    }
+                }
+            }
+            continue;
+        }
+        const uint32_t s = sval[(uint64_t)u * kLanes + lane];  // kInf: lane b does not send from u
+        for (uint64_t j0 = e_beg; j0 < e_end; j0 += 32) {
+            const uint32_t cnt = (uint32_t)min((uint64_t)32, e_end - j0);
+            uint32_t v_l = 0, w_l = 1;
+            if (lane < cnt) {
+                v_l = __ldg(col + j0 + lane);
+                if (kWeightKind == 1) w_l = __ldg(w8 + j0 + lane);
+                if (kWeightKind == 2) w_l = __ldg(w32 + j0 + lane);
+            }
+            for (uint32_t q = 0; q < cnt; ++q) {
+                const uint32_t v = __shfl_sync(0xFFFFFFFFu, v_l, q);
+                const uint32_t w = __shfl_sync(0xFFFFFFFFu, w_l, q);
+                bool changed = false;
+                if (s != kInf) {
+                    const uint32_t d = batch_cand(s, w, ctr);
+                    changed = d < atomicMin(&dist[(uint64_t)v * kLanes + lane], d);
+                }
+                const unsigned mask = __ballot_sync(0xFFFFFFFFu, changed);
+                if (mask && lane == 0) {
+                    const unsigned prev = atomicOr(&cmask[v], mask);
+                    if (prev == 0) next[atomicAdd(&ctr->next_size, 1u)] = v;
+                }
+            }
+        }
+    }
+}
+
 // previous senders: snapshot rows back to kInf
 __global__ void batch_reset_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl,
                                    uint32_t* __restrict__ sval, uint32_t* __restrict__ smask) {
@@ -238,13 +369,15 @@ __global__ void batch_apply_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl*
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long msgs = 0;
+    unsigned long long msgs = 0, edges = 0;
     for (uint64_t i = warp; i < f; i += nwarps) {
         const uint32_t v = F[i];
         const uint32_t mask = cmask[v];
         const bool mine = (mask >> lane) & 1u;
+        const uint64_t deg = off[v + 1] - off[v];
         sval[(uint64_t)v * kLanes + lane] = mine ? dist[(uint64_t)v * kLanes + lane] : kInf;
-        if (mine) msgs += off[v + 1] - off[v];
+        if (mine) msgs += deg;
+        edges += deg;
         __syncwarp();
         if (lane == 0) {
             smask[v] = mask;
@@ -252,11 +385,17 @@ __global__ void batch_apply_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl*
         }
     }
     if (msgs) atomicAdd(&ctr->msgs[lane], msgs);
+    if (lane == 0 && edges) atomicAdd(&ctr->edges, edges);
 }
 
 // the group's loop state after the seed: superstep 0 counts for every source,
 // superstep 1 for those whose source has out-edges
-__global__ void batch_init_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t k) {
+__device__ __forceinline__ bool batch_push_pick(unsigned long long edges, unsigned long long divisor, uint64_t m) {
+    return divisor > 0 && (double)edges * (double)divisor < (double)m;
+}
+
+__global__ void batch_init_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t k,
+                                  unsigned long long divisor, uint64_t m) {
     const uint32_t b = threadIdx.x;
     if (b < kLanes) {
         ctl->count[b] = b < k ? 1u + (ctr->msgs[b] > 0 ? 1u : 0u) : 0u;
@@ -269,8 +408,12 @@ __global__ void batch_init_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __r
         ctl->iter = 0;
         ctl->done = ctr->next_size == 0;
         ctl->status = 0;
+        ctl->divisor = divisor;
+        ctl->push = batch_push_pick(ctr->edges, divisor, m);
         ctr->next_size = 0;
         ctr->status = 0;
+        ctr->edges = 0;
+        ctr->ntasks = 0;
     }
 }
 
@@ -278,7 +421,7 @@ __global__ void batch_init_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __r
 // counters are cleared for the next superstep, and the WHILE condition says
 // whether the graph runs another one (not past kLoopCap in one launch).
 __global__ void batch_step_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t n,
-                                  cudaGraphConditionalHandle loop) {
+                                  uint64_t m, cudaGraphConditionalHandle loop) {
     const uint32_t b = threadIdx.x;
     if (b < kLanes) {
         if (ctr->msgs[b] > 0) ++ctl->count[b];
@@ -292,8 +435,11 @@ __global__ void batch_step_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __r
         ctl->status = status;
         ctl->f = fn <= n ? fn : 0u;
         ctl->cur ^= 1u;
+        ctl->push = batch_push_pick(ctr->edges, ctl->divisor, m);
         ctr->next_size = 0;
         ctr->status = 0;
+        ctr->edges = 0;
+        ctr->ntasks = 0;
         const bool more = ctl->f > 0 && status == 0;
         ctl->done = !more;
         const unsigned it = ctl->iter + 1;
@@ -340,6 +486,7 @@ struct BatchWorkspace {
     BatchCounters* ctr = nullptr;
     BatchCtl* ctl = nullptr;
     BatchCtl* h_ctl = nullptr;  // pinned mirror
+    unsigned long long* tasks = nullptr;  // push tasks of the current senders
     cudaGraphExec_t loop[3] = {nullptr, nullptr, nullptr};  // superstep loop, per weight kind
 };
 
@@ -356,6 +503,7 @@ void batch_free(ipg_graph* g) {
     cudaFree(b->src_int);
     cudaFree(b->ctr);
     cudaFree(b->ctl);
+    cudaFree(b->tasks);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
     for (int i = 0; i < 3; ++i)
         if (b->loop[i]) cudaGraphExecDestroy(b->loop[i]);
@@ -378,6 +526,9 @@ static ipg_status batch_prepare(ipg_graph* g, cudaStream_t st) {
     IPG_CUDA(cudaMalloc(&b->src_int, sizeof(uint32_t) * kLanes));
     IPG_CUDA(cudaMalloc(&b->ctr, sizeof(BatchCounters)));
     IPG_CUDA(cudaMalloc(&b->ctl, sizeof(BatchCtl)));
+    // a sender with d out-edges makes ceil(d / kPushChunk) <= d / kPushChunk + 1 tasks
+    const size_t max_tasks = (size_t)n + g->m / kPushChunk + 1;
+    IPG_CUDA(cudaMalloc(&b->tasks, sizeof(unsigned long long) * max_tasks));
     IPG_CUDA(cudaHostAlloc(&b->h_ctl, sizeof(BatchCtl), cudaHostAllocDefault));
     b->chunks = (g->m + kChunk - 1) / kChunk;
     IPG_CUDA(cudaMalloc(&b->chunk_row, sizeof(uint32_t) * (b->chunks ? b->chunks : 1)));
@@ -399,17 +550,26 @@ static void batch_superstep(ipg_graph* g, BatchWorkspace* b, int wkind, cudaGrap
     batch_pull_kernel<K><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,       \
                                                b->chunks, g->n, g->m, b->sval, b->smask, b->dist, b->cmask,      \
                                                b->fr[0], b->fr[1], b->ctl, b->ctr)
-    if (wkind == 1)
+#define IPG_BATCH_PUSH(K)                                                                                         \
+    batch_push_kernel<K><<<fixed, 256, 0, st>>>(g->off, g->col, g->w8, g->w, b->tasks, b->sval, b->smask, b->dist,  \
+                                                b->cmask, b->fr[0], b->fr[1], b->ctl, b->ctr)
+    batch_tasks_kernel<<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, g->off, b->tasks, b->ctr);
+    if (wkind == 1) {
         IPG_BATCH_PULL(1);
-    else if (wkind == 2)
+        IPG_BATCH_PUSH(1);
+    } else if (wkind == 2) {
         IPG_BATCH_PULL(2);
-    else
+        IPG_BATCH_PUSH(2);
+    } else {
         IPG_BATCH_PULL(0);
+        IPG_BATCH_PUSH(0);
+    }
 #undef IPG_BATCH_PULL
+#undef IPG_BATCH_PUSH
     batch_reset_kernel<<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, b->sval, b->smask);
     batch_apply_kernel<<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, g->n, g->off, b->dist, b->sval, b->smask,
                                               b->cmask, b->ctr);
-    batch_step_kernel<<<1, kLanes, 0, st>>>(b->ctl, b->ctr, g->n, loop);
+    batch_step_kernel<<<1, kLanes, 0, st>>>(b->ctl, b->ctr, g->n, g->m, loop);
 }
 
 // Builds the graph [WHILE (cond) { superstep }] for this workspace and weight kind.
@@ -468,7 +628,7 @@ static ipg_status batch_group(ipg_graph* g, const uint32_t* sources, uint32_t k,
     IPG_TRY(map_to_internal(g, b->src_int, k, st));
     batch_seed_kernel<<<1, kLanes, 0, st>>>(b->src_int, k, g->off, b->dist, b->sval, b->smask, b->fr[0], b->ctr);
     IPG_CUDA(cudaGetLastError());
-    batch_init_kernel<<<1, kLanes, 0, st>>>(b->ctl, b->ctr, k);
+    batch_init_kernel<<<1, kLanes, 0, st>>>(b->ctl, b->ctr, k, (unsigned long long)batch_divisor_for(g), g->m);
     IPG_CUDA(cudaGetLastError());
     IPG_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
     IPG_CUDA(cudaStreamSynchronize(st));

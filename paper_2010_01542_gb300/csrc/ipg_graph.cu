@@ -478,6 +478,9 @@ long long pull_divisor_for(const ipg_graph* g, bool sssp) {
 }
 long long pr_engine_for(const ipg_graph* g) { return g->tuned.pr ? g->tuned.pr_engine : tuning().pr_engine; }
 long long pr_carveout_for(const ipg_graph* g) { return g->tuned.pr ? g->tuned.pr_carveout : tuning().pr_carveout; }
+long long batch_divisor_for(const ipg_graph* g) {
+    return g->tuned.batch ? g->tuned.batch_divisor : tuning().batch_divisor;
+}
 
 // ---------------------------------------------------------------------------
 // creation
@@ -794,6 +797,11 @@ ipg_status ipg_set_tuning(const char* name, int64_t value) {
         tuning().combine_warp = value;
         return IPG_OK;
     }
+    if (!strcmp(name, "batch_divisor")) {
+        if (value < 0) return set_error(IPG_EINVAL, "ipg_set_tuning: batch_divisor must be >= 0");
+        tuning().batch_divisor = value;
+        return IPG_OK;
+    }
     if (!strcmp(name, "pr_engine")) {
         if (value != 0 && value != 1) return set_error(IPG_EINVAL, "ipg_set_tuning: pr_engine must be 0 or 1");
         tuning().pr_engine = value;
@@ -820,6 +828,10 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value) {
     }
     if (!strcmp(name, "combine_warp")) {
         *value = tuning().combine_warp;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "batch_divisor")) {
+        *value = tuning().batch_divisor;
         return IPG_OK;
     }
     if (!strcmp(name, "pr_engine")) {

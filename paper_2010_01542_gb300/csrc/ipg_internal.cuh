@@ -65,9 +65,9 @@ struct DeviceGuard {
 
 // knobs an autotuned graph carries instead of the process-wide ones
 struct GraphTuning {
-    bool pr = false, cc = false, sssp = false;
+    bool pr = false, cc = false, sssp = false, batch = false;
     long long pr_engine = 0, pr_carveout = -1;
-    long long cc_divisor = 6, sssp_divisor = 6;
+    long long cc_divisor = 6, sssp_divisor = 6, batch_divisor = 6;
 };
 
 // per-superstep CUDA events (IPG_STAT_TIMING)
@@ -183,6 +183,7 @@ struct Tuning {
     long long combine_warp = 0;  // general combiners: fold same-destination messages within a warp first
     long long pr_threads = 256;  // PageRank pull kernel: threads per CTA (256 or 512)
     long long pr_carveout = -1;  // PageRank pull kernel: shared-memory carveout percent (-1 = smallest)
+    long long batch_divisor = 6; // batched SSSP: push when the senders' out-edges < m / batch_divisor (0 = pull)
     long long pr_engine = 0;     // PageRank pull kernel: 0 staged messages, 1 direct (registers)
 };
 Tuning& tuning();
@@ -190,6 +191,7 @@ Tuning& tuning();
 long long pull_divisor_for(const ipg_graph* g, bool sssp);
 long long pr_engine_for(const ipg_graph* g);
 long long pr_carveout_for(const ipg_graph* g);
+long long batch_divisor_for(const ipg_graph* g);
 // stats helpers
 void stats_begin(ipg_stats* s);
 void stats_put(ipg_stats* s, uint32_t idx, const ipg_superstep_stats& rec);

@@ -22,10 +22,37 @@ __global__ void sample_offsets_kernel(const uint64_t* __restrict__ off, uint32_t
     if (i < kSamples) out[i] = off[(uint64_t)n * i / (kSamples - 1)];
 }
 
+enum Prog { kProgHashmin = 0, kProgSssp = 1, kProgPagerank = 2, kProgBatch = 3, kProgs = 4 };
+const uint32_t kProgBit[kProgs] = {IPG_TUNE_HASHMIN, IPG_TUNE_SSSP, IPG_TUNE_PAGERANK, IPG_TUNE_SSSP_BATCH};
+constexpr uint32_t kBatchSources = 32;
+
 struct CacheEntry {
     GraphTuning t;
-    float ms[3] = {0.f, 0.f, 0.f};  // hashmin, sssp, pagerank of the chosen candidates
+    float ms[kProgs] = {0.f, 0.f, 0.f, 0.f};  // the chosen candidates' runs
 };
+
+bool tuned(const GraphTuning& t, int prog) {
+    return prog == kProgHashmin ? t.cc : prog == kProgSssp ? t.sssp : prog == kProgPagerank ? t.pr : t.batch;
+}
+void untune(GraphTuning& t, int prog) {
+    if (prog == kProgHashmin) t.cc = false;
+    if (prog == kProgSssp) t.sssp = false;
+    if (prog == kProgPagerank) t.pr = false;
+    if (prog == kProgBatch) t.batch = false;
+}
+// candidate c of program prog; a and b are its values (b only for PageRank)
+void set_candidate(GraphTuning& t, int prog, long long a, long long b) {
+    if (prog == kProgHashmin) t.cc = true, t.cc_divisor = a;
+    if (prog == kProgSssp) t.sssp = true, t.sssp_divisor = a;
+    if (prog == kProgPagerank) t.pr = true, t.pr_engine = a, t.pr_carveout = b;
+    if (prog == kProgBatch) t.batch = true, t.batch_divisor = a;
+}
+void copy_choice(GraphTuning& dst, const GraphTuning& src, int prog) {
+    if (prog == kProgHashmin) set_candidate(dst, prog, src.cc_divisor, 0);
+    if (prog == kProgSssp) set_candidate(dst, prog, src.sssp_divisor, 0);
+    if (prog == kProgPagerank) set_candidate(dst, prog, src.pr_engine, src.pr_carveout);
+    if (prog == kProgBatch) set_candidate(dst, prog, src.batch_divisor, 0);
+}
 
 std::mutex g_cache_mu;
 std::map<std::vector<uint64_t>, CacheEntry>& cache() {
@@ -78,7 +105,7 @@ ipg_status best_of_two(cudaStream_t st, float* ms, uint32_t* runs, F&& call) {
 }
 
 ipg_status autotune(ipg_graph* g, uint32_t programs, uint32_t source, ipg_tune_report* rep, cudaStream_t st) {
-    const uint32_t kAll = IPG_TUNE_PAGERANK | IPG_TUNE_HASHMIN | IPG_TUNE_SSSP;
+    const uint32_t kAll = IPG_TUNE_PAGERANK | IPG_TUNE_HASHMIN | IPG_TUNE_SSSP | IPG_TUNE_SSSP_BATCH;
     if (!g) return set_error(IPG_EINVAL, "ipg_autotune: graph is NULL");
     if (programs & ~(kAll | IPG_TUNE_FORCE)) return set_error(IPG_EINVAL, "ipg_autotune: unknown program bits 0x%x", programs);
     if ((programs & IPG_TUNE_HASHMIN) && g->directed)
@@ -88,16 +115,18 @@ ipg_status autotune(ipg_graph* g, uint32_t programs, uint32_t source, ipg_tune_r
     const bool force = programs & IPG_TUNE_FORCE;
     programs &= kAll;
     ipg_tune_report r{};
-    r.hashmin_pull_divisor = r.sssp_pull_divisor = r.pr_engine = r.pr_carveout = -1;
+    r.hashmin_pull_divisor = r.sssp_pull_divisor = r.sssp_batch_divisor = r.pr_engine = r.pr_carveout = -1;
     const uint32_t n = g->n;
     if (n == 0 || programs == 0) {
         if (rep) *rep = r;
         return IPG_OK;
     }
+    const size_t words = (size_t)n * ((programs & IPG_TUNE_SSSP_BATCH) ? kBatchSources : 1);
     void* scratch = nullptr;
-    IPG_CUDA(cudaMalloc(&scratch, sizeof(uint32_t) * (n > (uint32_t)(2 * kSamples) ? n : 2 * kSamples)));
+    IPG_CUDA(cudaMalloc(&scratch, sizeof(uint32_t) * (words > 2 * kSamples ? words : 2 * kSamples)));
     ipg_status rc = IPG_OK;
     GraphTuning t = g->tuned;
+    float best_ms[kProgs] = {0.f, 0.f, 0.f, 0.f}, def_ms[kProgs] = {0.f, 0.f, 0.f, 0.f};
     do {
         std::vector<uint64_t> key;
         rc = fingerprint(g, static_cast<uint64_t*>(scratch), st, &key);
@@ -112,84 +141,82 @@ ipg_status autotune(ipg_graph* g, uint32_t programs, uint32_t source, ipg_tune_r
                 have = true;
             }
         }
-        uint32_t from_cache = 0;
         // SSSP source: the caller's, else the vertex of largest total degree (internal id 0)
         uint32_t src = source;
-        if ((programs & IPG_TUNE_SSSP) && src >= n) {
+        if ((programs & (IPG_TUNE_SSSP | IPG_TUNE_SSSP_BATCH)) && src >= n) {
             cudaError_t e = cudaMemcpy(&src, g->perm, sizeof(uint32_t), cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) {
                 rc = cuda_fail(e, "copy of the tuning source", __FILE__, __LINE__);
                 break;
             }
         }
+        uint32_t batch_src[kBatchSources];
+        batch_src[0] = src;
+        for (uint32_t i = 1; i < kBatchSources; ++i) batch_src[i] = (uint32_t)((uint64_t)n * i / kBatchSources);
         uint32_t* out_u = static_cast<uint32_t*>(scratch);
         float* out_f = static_cast<float*>(scratch);
-        for (int prog = 0; prog < 3 && rc == IPG_OK; ++prog) {
-            const uint32_t bit = prog == 0 ? IPG_TUNE_HASHMIN : prog == 1 ? IPG_TUNE_SSSP : IPG_TUNE_PAGERANK;
-            if (!(programs & bit)) continue;
-            const bool cached = have && (prog == 0 ? hit.t.cc : prog == 1 ? hit.t.sssp : hit.t.pr);
-            if (cached) {
+        uint32_t from_cache = 0, requested = 0;
+        for (int prog = 0; prog < kProgs && rc == IPG_OK; ++prog) {
+            if (!(programs & kProgBit[prog])) continue;
+            ++requested;
+            if (have && tuned(hit.t, prog)) {
                 ++from_cache;
-                if (prog == 0) t.cc = true, t.cc_divisor = hit.t.cc_divisor;
-                if (prog == 1) t.sssp = true, t.sssp_divisor = hit.t.sssp_divisor;
-                if (prog == 2) t.pr = true, t.pr_engine = hit.t.pr_engine, t.pr_carveout = hit.t.pr_carveout;
-                (prog == 0 ? r.hashmin_ms : prog == 1 ? r.sssp_ms : r.pagerank_ms) = hit.ms[prog];
+                copy_choice(t, hit.t, prog);
+                best_ms[prog] = hit.ms[prog];
                 continue;
             }
             auto run = [&]() -> ipg_status {
-                if (prog == 0) return ipg_hashmin_cc_dev(g, out_u, nullptr, st);
-                if (prog == 1) return ipg_sssp_dev(g, src, out_u, nullptr, st);
+                if (prog == kProgHashmin) return ipg_hashmin_cc_dev(g, out_u, nullptr, st);
+                if (prog == kProgSssp) return ipg_sssp_dev(g, src, out_u, nullptr, st);
+                if (prog == kProgBatch) return sssp_batch_run(g, batch_src, kBatchSources, out_u, nullptr, st);
                 return ipg_pagerank_dev(g, 3, out_f, nullptr, st);
             };
             // the process-wide knobs first (also a warm-up: workspaces, in-edge copy)
-            GraphTuning saved = g->tuned;
-            if (prog == 0) g->tuned.cc = false;
-            if (prog == 1) g->tuned.sssp = false;
-            if (prog == 2) g->tuned.pr = false;
+            const GraphTuning saved = g->tuned;
+            untune(g->tuned, prog);
             rc = run();
-            float def_ms = 0.f;
-            if (rc == IPG_OK) rc = best_of_two(st, &def_ms, &r.candidates_timed, run);
+            if (rc == IPG_OK) rc = best_of_two(st, &def_ms[prog], &r.candidates_timed, run);
             float best = -1.f;
             long long best_a = 0, best_b = 0;
-            const int count = prog == 2 ? 4 : (int)(sizeof(kDivisors) / sizeof(kDivisors[0]));
+            const int count = prog == kProgPagerank ? 4 : (int)(sizeof(kDivisors) / sizeof(kDivisors[0]));
             for (int c = 0; c < count && rc == IPG_OK; ++c) {
-                if (prog == 0) g->tuned.cc = true, g->tuned.cc_divisor = kDivisors[c];
-                if (prog == 1) g->tuned.sssp = true, g->tuned.sssp_divisor = kDivisors[c];
-                if (prog == 2) g->tuned.pr = true, g->tuned.pr_engine = kPrShapes[c][0], g->tuned.pr_carveout = kPrShapes[c][1];
+                const long long a = prog == kProgPagerank ? kPrShapes[c][0] : kDivisors[c];
+                const long long b = prog == kProgPagerank ? kPrShapes[c][1] : 0;
+                set_candidate(g->tuned, prog, a, b);
                 float ms = 0.f;
                 rc = best_of_two(st, &ms, &r.candidates_timed, run);
                 if (rc == IPG_OK && (best < 0.f || ms < best)) {
                     best = ms;
-                    best_a = prog == 2 ? kPrShapes[c][0] : kDivisors[c];
-                    best_b = prog == 2 ? kPrShapes[c][1] : 0;
+                    best_a = a;
+                    best_b = b;
                 }
             }
             g->tuned = saved;
             if (rc != IPG_OK) break;
-            if (prog == 0) t.cc = true, t.cc_divisor = best_a, r.hashmin_ms = best, r.hashmin_default_ms = def_ms;
-            if (prog == 1) t.sssp = true, t.sssp_divisor = best_a, r.sssp_ms = best, r.sssp_default_ms = def_ms;
-            if (prog == 2) {
-                t.pr = true, t.pr_engine = best_a, t.pr_carveout = best_b;
-                r.pagerank_ms = best, r.pagerank_default_ms = def_ms;
-            }
+            set_candidate(t, prog, best_a, best_b);
+            best_ms[prog] = best;
             std::lock_guard<std::mutex> lock(g_cache_mu);
             CacheEntry& ce = cache()[key];
-            if (prog == 0) ce.t.cc = true, ce.t.cc_divisor = best_a;
-            if (prog == 1) ce.t.sssp = true, ce.t.sssp_divisor = best_a;
-            if (prog == 2) ce.t.pr = true, ce.t.pr_engine = best_a, ce.t.pr_carveout = best_b;
+            set_candidate(ce.t, prog, best_a, best_b);
             ce.ms[prog] = best;
         }
         if (rc != IPG_OK) break;
         g->tuned = t;
-        r.cached = from_cache > 0 && from_cache == (uint32_t)__builtin_popcount(programs);
+        r.cached = from_cache > 0 && from_cache == requested;
     } while (false);
     cudaFree(scratch);
     if (rc != IPG_OK) return rc;
-    r.programs = (g->tuned.pr ? IPG_TUNE_PAGERANK : 0u) | (g->tuned.cc ? IPG_TUNE_HASHMIN : 0u) |
-                 (g->tuned.sssp ? IPG_TUNE_SSSP : 0u);
-    if (g->tuned.cc) r.hashmin_pull_divisor = g->tuned.cc_divisor;
-    if (g->tuned.sssp) r.sssp_pull_divisor = g->tuned.sssp_divisor;
-    if (g->tuned.pr) r.pr_engine = g->tuned.pr_engine, r.pr_carveout = g->tuned.pr_carveout;
+    const GraphTuning& gt = g->tuned;
+    r.programs = (gt.pr ? IPG_TUNE_PAGERANK : 0u) | (gt.cc ? IPG_TUNE_HASHMIN : 0u) | (gt.sssp ? IPG_TUNE_SSSP : 0u) |
+                 (gt.batch ? IPG_TUNE_SSSP_BATCH : 0u);
+    if (gt.cc) r.hashmin_pull_divisor = gt.cc_divisor;
+    if (gt.sssp) r.sssp_pull_divisor = gt.sssp_divisor;
+    if (gt.batch) r.sssp_batch_divisor = gt.batch_divisor;
+    if (gt.pr) r.pr_engine = gt.pr_engine, r.pr_carveout = gt.pr_carveout;
+    r.hashmin_ms = best_ms[kProgHashmin], r.hashmin_default_ms = def_ms[kProgHashmin];
+    r.sssp_ms = best_ms[kProgSssp], r.sssp_default_ms = def_ms[kProgSssp];
+    r.sssp_batch_ms = best_ms[kProgBatch], r.sssp_batch_default_ms = def_ms[kProgBatch];
+    r.pagerank_ms = best_ms[kProgPagerank], r.pagerank_default_ms = def_ms[kProgPagerank];
     if (rep) *rep = r;
     return IPG_OK;
 }

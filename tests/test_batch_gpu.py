@@ -25,6 +25,16 @@ def ipg():
     return ipg
 
 
+@pytest.fixture(autouse=True, params=["auto", "pull", "push"])
+def batch_direction(request, ipg):
+    """Every batched SSSP test runs with the automatic push/pull switch, pull only
+    (batch_divisor 0) and push whenever the senders hold fewer than all m edges (1)."""
+    old = ipg.ipg_get_tuning("batch_divisor")
+    ipg.ipg_set_tuning("batch_divisor", {"auto": old, "pull": 0, "push": 1}[request.param])
+    yield request.param
+    ipg.ipg_set_tuning("batch_divisor", old)
+
+
 def _check_batch(ipg, g, sources, weights, use_oracle=False):
     h = ipg.ipg_graph_create(g.offsets, g.cols, weights, g.n, g.m, g.directed)
     dist, steps = ipg.ipg_sssp_batch(h, sources)

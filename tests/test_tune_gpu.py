@@ -58,10 +58,14 @@ def test_autotune_keeps_results(ipg, name, spec):
     src = gen.max_out_degree_vertex(g)
     hashmin = spec["undirected"]
     before = _results(ipg, h, g, src, hashmin)
-    progs = ipg.IPG_TUNE_PAGERANK | ipg.IPG_TUNE_SSSP | (ipg.IPG_TUNE_HASHMIN if hashmin else 0)
+    batch_src = np.random.default_rng(1).integers(0, g.n, size=40).astype(np.uint32)
+    before["batch"], before["batch_steps"] = ipg.ipg_sssp_batch(h, batch_src)
+    progs = ipg.IPG_TUNE_PAGERANK | ipg.IPG_TUNE_SSSP | ipg.IPG_TUNE_SSSP_BATCH | \
+        (ipg.IPG_TUNE_HASHMIN if hashmin else 0)
     rep = ipg.ipg_autotune(h, progs | ipg.IPG_TUNE_FORCE, src)
     assert rep["programs"] == progs and rep["cached"] == 0 and rep["candidates_timed"] > 0
-    assert rep["sssp_pull_divisor"] in DIVISORS
+    assert rep["sssp_pull_divisor"] in DIVISORS and rep["sssp_batch_divisor"] in DIVISORS
+    assert rep["sssp_batch_ms"] > 0
     assert (rep["pr_engine"], rep["pr_carveout"]) in PR_SHAPES
     if hashmin:
         assert rep["hashmin_pull_divisor"] in DIVISORS
@@ -69,6 +73,7 @@ def test_autotune_keeps_results(ipg, name, spec):
         assert rep["hashmin_pull_divisor"] == -1
     assert rep["pagerank_ms"] > 0 and rep["sssp_ms"] > 0
     after = _results(ipg, h, g, src, hashmin)
+    after["batch"], after["batch_steps"] = ipg.ipg_sssp_batch(h, batch_src)
     for k in before:
         assert np.array_equal(np.asarray(before[k]), np.asarray(after[k])), k
     # a second call and an identical graph come from the cache
@@ -77,9 +82,10 @@ def test_autotune_keeps_results(ipg, name, spec):
     h2 = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, not spec["undirected"])
     rep2 = ipg.ipg_autotune(h2, progs, src)
     assert rep2["cached"] == 1 and rep2["candidates_timed"] == 0
-    assert (rep2["sssp_pull_divisor"], rep2["pr_engine"], rep2["pr_carveout"]) == \
-           (rep["sssp_pull_divisor"], rep["pr_engine"], rep["pr_carveout"])
+    for k in ("sssp_pull_divisor", "sssp_batch_divisor", "pr_engine", "pr_carveout", "hashmin_pull_divisor"):
+        assert rep2[k] == rep[k], k
     after2 = _results(ipg, h2, g, src, hashmin)
+    after2["batch"], after2["batch_steps"] = ipg.ipg_sssp_batch(h2, batch_src)
     for k in before:
         assert np.array_equal(np.asarray(before[k]), np.asarray(after2[k])), k
     h.destroy()
