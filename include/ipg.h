@@ -340,7 +340,21 @@ typedef struct {
     uint32_t max_batch;         /* SSSP queries dispatched together at most; 0 -> 256 */
     uint64_t workspace_budget;  /* bytes of graph workspace held at once; 0 -> free memory */
     uint64_t reserve_bytes;     /* device memory kept free when budget is 0; 0 -> 1 GiB */
+    uint32_t min_sssp_batch;    /* fewer queued SSSP queries run one source at a time; 0 -> 16 */
+    uint32_t flags;             /* IPG_SERVER_* bits */
 } ipg_server_options;
+
+/* ipg_server_create runs ipg_autotune on every graph before it starts serving
+ * (PageRank, SSSP, batched SSSP, and Hashmin on undirected graphs); a graph
+ * already tuned for a program keeps its values.  Tuning times each graph alone;
+ * under concurrent load other choices can be faster, so it is off by default. */
+#define IPG_SERVER_AUTOTUNE 1u
+/* ipg_server_create runs every program the server dispatches once on every graph
+ * (one SSSP, one batched SSSP of 32 sources, one PageRank update, and Hashmin on
+ * undirected graphs) into a scratch buffer, so that the graphs' device
+ * workspaces exist before the first query instead of being allocated while
+ * queries wait.  With a workspace budget, workers may release them later. */
+#define IPG_SERVER_PREPARE 2u
 
 /* graphs: count graph handles (all on the same device); opt may be NULL. */
 ipg_status ipg_server_create(ipg_graph* const* graphs, uint32_t count, const ipg_server_options* opt,

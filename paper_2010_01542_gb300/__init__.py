@@ -577,9 +577,13 @@ class _CCompletion(ctypes.Structure):
                 ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
+IPG_SERVER_AUTOTUNE = 1
+IPG_SERVER_PREPARE = 2
+
+
 class _COptions(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_uint32), ("max_batch", ctypes.c_uint32), ("workspace_budget", ctypes.c_uint64),
-                ("reserve_bytes", ctypes.c_uint64)]
+                ("reserve_bytes", ctypes.c_uint64), ("min_sssp_batch", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 @dataclass
@@ -600,7 +604,8 @@ class Server:
     completion is polled."""
 
     def __init__(self, graphs, workers: int = 0, max_batch: int = 0, workspace_budget: int = 0,
-                 reserve_bytes: int = 0):
+                 reserve_bytes: int = 0, min_sssp_batch: int = 0, autotune: bool = False,
+                 prepare: bool = False):
         lib = load_library()
         self._lib = lib
         self._graphs = list(graphs)
@@ -618,7 +623,8 @@ class Server:
         lib.ipg_server_destroy.argtypes = [ctypes.c_void_p]
         lib.ipg_server_destroy.restype = None
         handles = (ctypes.c_void_p * len(self._graphs))(*[g.handle for g in self._graphs])
-        opt = _COptions(workers, max_batch, workspace_budget, reserve_bytes)
+        opt = _COptions(workers, max_batch, workspace_budget, reserve_bytes, min_sssp_batch,
+                        (IPG_SERVER_AUTOTUNE if autotune else 0) | (IPG_SERVER_PREPARE if prepare else 0))
         h = ctypes.c_void_p()
         _check(lib.ipg_server_create(handles, len(self._graphs), ctypes.byref(opt), ctypes.byref(h)))
         self._h = h

@@ -6,8 +6,9 @@
 // workspace and must not overlap) and dispatch:
 //   - all of that graph's queued SSSP queries together, up to max_batch, through
 //     the batched SSSP engine (queries that arrived while the previous dispatch
-//     was on the GPU join the next one: continuous batching); below 8 queries
-//     the dispatch runs them one source at a time, which is faster there;
+//     was on the GPU join the next one: continuous batching); below
+//     min_sssp_batch queries (16 by default) the dispatch runs them one source
+//     at a time, which is faster there;
 //   - otherwise the head query's kind (Hashmin, or PageRank with the same update
 //     count): every such query queued on the graph shares one run, since they
 //     compute the same result (in flight only: finished results are not reused).
@@ -52,6 +53,8 @@ struct ipg_server {
     size_t budget = 0;  // 0: use free device memory minus reserve
     size_t reserve = 0;
     uint32_t max_batch = 256;
+    uint32_t min_batch = 16;  // fewer queued SSSP queries run one source at a time
+    size_t stage_words = 0;   // per-worker staging allocated at start (IPG_SERVER_PREPARE)
     std::chrono::steady_clock::time_point t0;
     int device = 0;
 
@@ -66,13 +69,42 @@ void release_workspace(ipg_graph* g);  // ipg_graph.cu
 
 namespace {
 
-// fewer queued SSSP queries than this run one source at a time (measured break-even of
-// the batched engine against one-source runs is about 8-12 sources on R-MAT 22/16)
-constexpr size_t kMinSsspBatch = 8;
+// default for ipg_server_options.min_sssp_batch: fewer queued SSSP queries than this
+// run one source at a time.  A batched group costs about as much whatever its
+// size up to 32 sources (29 ms on R-MAT 22/16 against 1.7 ms per one-source run),
+// so batching pays from about 16 queued queries.
+constexpr uint32_t kMinSsspBatch = 16;
+
+// one run of every program on every graph, so their workspaces exist before serving
+ipg_status prepare_graphs(ipg_graph* const* graphs, uint32_t count) {
+    size_t nmax = 0;
+    for (uint32_t i = 0; i < count; ++i) nmax = graphs[i]->n > nmax ? graphs[i]->n : nmax;
+    if (!nmax) return IPG_OK;
+    constexpr uint32_t kSources = 32;
+    uint32_t* scratch = nullptr;
+    IPG_CUDA(cudaMalloc(&scratch, sizeof(uint32_t) * kSources * nmax));
+    ipg_status r = IPG_OK;
+    for (uint32_t i = 0; i < count && r == IPG_OK; ++i) {
+        ipg_graph* g = graphs[i];
+        if (!g->n) continue;
+        uint32_t src[kSources];
+        for (uint32_t k = 0; k < kSources; ++k) src[k] = (uint32_t)((uint64_t)g->n * k / kSources);
+        r = ipg_sssp_dev(g, 0, scratch, nullptr, g->stream);
+        if (r == IPG_OK) r = sssp_batch_run(g, src, kSources, scratch, nullptr, g->stream);
+        if (r == IPG_OK) r = ipg_pagerank_dev(g, 1, reinterpret_cast<float*>(scratch), nullptr, g->stream);
+        if (r == IPG_OK && !g->directed) r = ipg_hashmin_cc_dev(g, scratch, nullptr, g->stream);
+        // the host-output staging of ipg_sssp / ipg_hashmin_cc / ipg_pagerank
+        size_t cap = g->val_stage ? (size_t)g->n * sizeof(uint32_t) : 0;
+        if (r == IPG_OK && !g->val_stage) r = ensure(&g->val_stage, &cap, (size_t)g->n);
+        if (r == IPG_OK) r = ensure(&g->pr_out_stage, &g->pr_out_stage_cap, (size_t)g->n);
+    }
+    cudaFree(scratch);
+    return r;
+}
 
 
 // device bytes a dispatch may still need to allocate on this graph
-size_t workspace_need(const ipg_graph* g, uint32_t kind, uint32_t k) {
+size_t workspace_need(const ipg_graph* g, uint32_t kind, uint32_t k, uint32_t min_batch) {
     const size_t n = g->n, m = g->m;
     const size_t tiles = (n + m) / 2048 + 2;
     size_t need = 0;
@@ -82,7 +114,8 @@ size_t workspace_need(const ipg_graph* g, uint32_t kind, uint32_t k) {
     } else {
         if (!g->stamp) need += n * 36 + tiles * 4;
         if (!g->sval) need += n * 4 + tiles * 12;
-        if (kind == IPG_Q_SSSP && k >= kMinSsspBatch && !g->batch) need += n * 264;
+        // batched SSSP: dist and sender rows [n][32], masks, frontiers, push tasks, chunk rows
+        if (kind == IPG_Q_SSSP && k >= min_batch && !g->batch) need += n * 280 + (m / 256 + 1) * 12;
     }
     if (!g->val_stage) need += n * 4;
     return need;
@@ -98,9 +131,22 @@ size_t device_free(int device) {
     return fr;
 }
 
+// sources a worker stages at once for batched SSSP (the batched engine's group size)
+constexpr size_t kStageSources = 32;
+
 struct WorkerBuffers {
-    uint32_t* dev = nullptr;  // k * n staging for batched SSSP
+    uint32_t* dev = nullptr;  // kStageSources * n staging for batched SSSP
     size_t cap = 0;
+    ipg_status reserve(size_t words) {
+        if (cap >= words) return IPG_OK;
+        if (dev) cudaFree(dev);
+        dev = nullptr;
+        cap = 0;
+        if (cudaMalloc(&dev, sizeof(uint32_t) * (words ? words : 1)) != cudaSuccess)
+            return set_error(IPG_ENOMEM, "server: staging allocation failed");
+        cap = words;
+        return IPG_OK;
+    }
     ~WorkerBuffers() {
         if (dev) cudaFree(dev);
     }
@@ -124,6 +170,7 @@ void finish(ipg_server* s, const std::vector<ipg_server::Pending>& batch, const 
 void worker_main(ipg_server* s) {
     cudaSetDevice(s->device);
     WorkerBuffers buf;
+    if (s->stage_words) buf.reserve(s->stage_words);  // IPG_SERVER_PREPARE: before any query
     std::unique_lock<std::mutex> lock(s->mu);
     while (!s->stop) {
         // the idle graph whose head query has waited longest
@@ -167,7 +214,7 @@ void worker_main(ipg_server* s) {
             }
         }
         // admission by device memory
-        const size_t need = workspace_need(slot.g, kind, (uint32_t)batch.size());
+        const size_t need = workspace_need(slot.g, kind, (uint32_t)batch.size(), s->min_batch);
         for (;;) {
             size_t avail;
             if (s->budget) {
@@ -200,7 +247,7 @@ void worker_main(ipg_server* s) {
         slot.last_used = ++s->tick;
         slot.held += need;
         ipg_graph* g = slot.g;
-        const bool batched = kind == IPG_Q_SSSP && batch.size() >= kMinSsspBatch;
+        const bool batched = kind == IPG_Q_SSSP && batch.size() >= s->min_batch;
         lock.unlock();
 
         const double t_start = s->now();
@@ -215,28 +262,23 @@ void worker_main(ipg_server* s) {
                 steps[i] = st.count;
             }
         } else if (kind == IPG_Q_SSSP) {
+            // groups of kStageSources (the engine's group size) through a staging buffer
             const size_t k = batch.size(), n = g->n;
-            ipg_status r = IPG_OK;
-            if (buf.cap < k * n) {
-                if (buf.dev) cudaFree(buf.dev);
-                buf.dev = nullptr;
-                buf.cap = 0;
-                if (cudaMalloc(&buf.dev, sizeof(uint32_t) * (k * n ? k * n : 1)) != cudaSuccess)
-                    r = set_error(IPG_ENOMEM, "server: staging allocation failed");
-                else
-                    buf.cap = k * n;
-            }
+            ipg_status r = buf.reserve(kStageSources * n);
             std::vector<uint32_t> src(k);
             for (size_t i = 0; i < k; ++i) src[i] = batch[i].q.source;
-            if (r == IPG_OK) r = sssp_batch_run(g, src.data(), (uint32_t)k, buf.dev, steps.data(), g->stream);
-            for (size_t i = 0; i < k && r == IPG_OK; ++i) {
-                cudaError_t e = cudaMemcpyAsync(batch[i].q.out, buf.dev + i * n, sizeof(uint32_t) * n,
-                                                cudaMemcpyDeviceToHost, g->stream);
-                if (e != cudaSuccess) r = cuda_fail(e, "server result copy", __FILE__, __LINE__);
-            }
-            if (r == IPG_OK) {
-                cudaError_t e = cudaStreamSynchronize(g->stream);
-                if (e != cudaSuccess) r = cuda_fail(e, "server result copy", __FILE__, __LINE__);
+            for (size_t i0 = 0; i0 < k && r == IPG_OK; i0 += kStageSources) {
+                const size_t kk = k - i0 < kStageSources ? k - i0 : kStageSources;
+                r = sssp_batch_run(g, src.data() + i0, (uint32_t)kk, buf.dev, steps.data() + i0, g->stream);
+                for (size_t i = 0; i < kk && r == IPG_OK; ++i) {
+                    cudaError_t e = cudaMemcpyAsync(batch[i0 + i].q.out, buf.dev + i * n, sizeof(uint32_t) * n,
+                                                    cudaMemcpyDeviceToHost, g->stream);
+                    if (e != cudaSuccess) r = cuda_fail(e, "server result copy", __FILE__, __LINE__);
+                }
+                if (r == IPG_OK) {
+                    cudaError_t e = cudaStreamSynchronize(g->stream);
+                    if (e != cudaSuccess) r = cuda_fail(e, "server result copy", __FILE__, __LINE__);
+                }
             }
             std::fill(rc.begin(), rc.end(), r);
         } else if (kind == IPG_Q_HASHMIN || kind == IPG_Q_PAGERANK) {
@@ -287,6 +329,28 @@ ipg_status ipg_server_create(ipg_graph* const* graphs, uint32_t count, const ipg
     s->max_batch = opt && opt->max_batch ? opt->max_batch : 256;
     s->budget = opt ? (size_t)opt->workspace_budget : 0;
     s->reserve = opt && opt->reserve_bytes ? (size_t)opt->reserve_bytes : ((size_t)1 << 30);
+    s->min_batch = opt && opt->min_sssp_batch ? opt->min_sssp_batch : kMinSsspBatch;
+    if (opt && (opt->flags & IPG_SERVER_PREPARE)) {
+        const ipg_status r = prepare_graphs(graphs, count);
+        if (r != IPG_OK) {
+            delete s;
+            return r;
+        }
+        for (uint32_t i = 0; i < count; ++i)
+            s->stage_words = std::max(s->stage_words, kStageSources * (size_t)graphs[i]->n);
+    }
+    if (opt && (opt->flags & IPG_SERVER_AUTOTUNE)) {
+        for (uint32_t i = 0; i < count; ++i) {
+            ipg_graph* g = graphs[i];
+            const uint32_t progs = IPG_TUNE_PAGERANK | IPG_TUNE_SSSP | IPG_TUNE_SSSP_BATCH |
+                                   (g->directed ? 0u : IPG_TUNE_HASHMIN);
+            const ipg_status r = ipg_autotune(g, progs, UINT32_MAX, nullptr, g->stream);
+            if (r != IPG_OK) {
+                delete s;
+                return r;
+            }
+        }
+    }
     for (uint32_t w = 0; w < workers; ++w) s->workers.emplace_back(worker_main, s);
     *out = s;
     return IPG_OK;

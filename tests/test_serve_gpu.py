@@ -51,8 +51,16 @@ def _mixed_queries(graphs, count, seed):
     return qs
 
 
+SERVER_MODES = {
+    "default": {},
+    "prepared-min4": dict(prepare=True, min_sssp_batch=4),  # workspaces made up front; batch from 4 queries
+    "autotuned": dict(autotune=True),                      # every graph tuned first: same results
+}
+
+
+@pytest.mark.parametrize("mode", sorted(SERVER_MODES))
 @pytest.mark.parametrize("budget", [0, 1 << 22])
-def test_results_same_alone_and_in_the_mix(ipg, budget):
+def test_results_same_alone_and_in_the_mix(ipg, budget, mode):
     graphs = _graph_set()
     handles = [ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, False) for g in graphs]
     queries = _mixed_queries(graphs, 300, seed=budget % 7 + 1)
@@ -61,7 +69,7 @@ def test_results_same_alone_and_in_the_mix(ipg, budget):
     for u, gi, kind, src in queries:
         vals, cnt, _ = _alone(ipg, handles[gi], kind, src)
         ref[u] = (vals.copy(), cnt)
-    srv = ipg.Server(handles, workers=4, max_batch=64, workspace_budget=budget)
+    srv = ipg.Server(handles, workers=4, max_batch=64, workspace_budget=budget, **SERVER_MODES[mode])
     done = []
     for u, gi, kind, src in queries:
         out = np.empty(graphs[gi].n, dtype=np.float32 if kind == 2 else np.uint32)
