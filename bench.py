@@ -45,8 +45,11 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["billion", "batch", "cc-batch", "serve"], default="billion",
-                   help="billion: the default bench line; batch: 256-source batched SSSP vs one at a time; "
+    p.add_argument("--workload", choices=["billion", "pagerank16", "hashmin20", "batch", "cc-batch", "serve"],
+                   default="billion",
+                   help="billion: the default bench line; pagerank16: PageRank on directed R-MAT 16/16; "
+                        "hashmin20: Hashmin components on undirected R-MAT 20/16; "
+                        "batch: 256-source batched SSSP vs one at a time; "
                         "cc-batch: 64 uneven Hashmin graphs in one object vs one at a time; "
                         "serve: Poisson stream of mixed queries on 32 resident graphs")
     p.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
@@ -531,6 +534,112 @@ def cc_batch_scales(count, seed):
     return [10 + gen.splitmix64((base + i) & 0xFFFFFFFFFFFFFFFF) % 11 for i in range(count)]
 
 
+def run_small_config(a, kind):
+    """One small configuration on one GPU, graph resident:
+    pagerank16  PageRank, 10 supersteps, directed R-MAT scale 16 EF 16 (value: GTEPS = 10 m / t);
+    hashmin20   Hashmin components to quiescence, undirected R-MAT scale 20 EF 16
+                (value: GTEPS = messages sent / t).
+    Per-superstep CUDA events give the dominant kernel's roofline; the oracle runs on the
+    whole graph on one host core for the CPU baseline.  With several ranks every rank runs
+    a replica."""
+    import torch
+
+    import gen
+    import oracle
+    import paper_2010_01542_gb300 as ipg
+
+    world, rank, local = dist_init(a)
+    ipg.load_library()
+    pr = kind == "pagerank16"
+    scale, ef = (16, 16) if pr else (20, 16)
+    g = gen.rmat(scale, ef, seed=a.seed, undirected=not pr)
+    h = ipg.ipg_graph_create(g.offsets, g.cols, None, g.n, g.m, pr)
+    stream = torch.cuda.Stream()
+    out = torch.empty(g.n, dtype=torch.float32 if pr else torch.int32, device="cuda")
+    tune = None
+    if not a.no_autotune:
+        tune = ipg.ipg_autotune(h, ipg.IPG_TUNE_PAGERANK if pr else ipg.IPG_TUNE_HASHMIN, stream=stream)
+        tune = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tune.items()}
+
+    # PageRank's timed steps run without per-superstep events, as one captured graph; a
+    # separate run with events gives the pull kernel's time for the roofline
+    def step(timing=not pr):
+        flags = ipg.IPG_STAT_TIMING if timing else 0
+        if pr:
+            return ipg.ipg_pagerank_dev(h, PR_UPDATES, out, stats_flags=flags, stream=stream)
+        return ipg.ipg_hashmin_cc_dev(h, out, stats_flags=flags, stream=stream)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    barrier(world)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    runs = [step() for _ in range(a.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    count, st = runs[-1]
+    edges = PR_UPDATES * g.m if pr else sum(s.messages_sent for s in st)
+    rate, ms_max = replica_throughput(edges * a.steps, ms, world)
+    # roofline of the step's dominant kernel (PageRank pull / pull-min or push relax)
+    peak, peak_kind = peak_hbm()
+    timed_runs = runs if not pr else [step(timing=True) for _ in range(3)]
+    recs = [s for _, sts in timed_runs for s in sts if s.flags & ipg.IPG_STAT_TIMING]
+    if pr:
+        byts = 8 * g.m + 24 * g.n
+        kern = {"pr_pull_kernel": (len(recs), sum(s.kernel_ms for s in recs), byts)}
+        rule = "8 m + 24 n per launch"
+    else:
+        kern = {}
+        for name, want in (("push_relax_kernel", False), ("pull_min_kernel", True)):
+            rr = [s for s in recs if s.senders and bool(s.flags & ipg.IPG_STAT_PULL) == want]
+            if rr:
+                kern[name] = (len(rr), sum(s.kernel_ms for s in rr),
+                              statistics.mean(8 * s.messages_sent + 16 * s.senders for s in rr))
+        rule = "8 B per message (4 B column + 4 B value RMW) + 16 B per sender"
+    dom = max(kern, key=lambda k: kern[k][1])
+    nl, kms, bpl = kern[dom]
+    achieved = bpl * nl / (kms / 1e3) / 1e9
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        t0 = time.perf_counter()
+        ref = oracle.pagerank(g.n, g.offsets, g.cols, PR_UPDATES) if pr else oracle.hashmin(g.n, g.offsets, g.cols)
+        t = time.perf_counter() - t0
+        host = out.cpu().numpy()
+        if pr:
+            ok = float(np.max(np.abs(host.astype(np.float64) - ref.values)) / ref.values.max()) <= 1e-5
+        else:
+            ok = bool(np.array_equal(host.view(np.uint32), ref.values))
+        ok = ok and ref.supersteps == count
+        cpu_edges = sum(s.messages_sent for s in ref.stats)
+        cpu = {"value": round(cpu_edges / t / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the whole graph: oracle {'PageRank 10 updates' if pr else 'Hashmin to quiescence'}, "
+                         f"{cpu_edges} messages in {t:.2f} s; GPU result matches the oracle: {ok}"}
+    if rank == 0:
+        line = {"metric": ("GTEPS, PageRank 10 supersteps" if pr else "GTEPS, Hashmin components to quiescence"),
+                "value": round(rate / 1e9, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": round(ms_max / a.steps, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+u32" if pr else "u32", "data": "synthetic",
+                "config": {"workload": (f"rmat{scale}-ef{ef} {'directed' if pr else 'undirected'} seed {a.seed}: "
+                                        + ("PageRank 10 supersteps" if pr else "Hashmin components")),
+                           "n": g.n, "m": g.m, "supersteps": count,
+                           "l2": "graph L2-resident: latency- and launch-bound at this size"},
+                "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                             "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                             "traffic": None, "algorithmic_bytes_per_launch": int(bpl), "bytes_rule": rule},
+                "cpu_baseline": cpu, "autotune": tune, "clocks": clocks,
+                "gpu_launches": ((1 + 2 * PR_UPDATES + 1) if pr else
+                                 (1 + 5 * sum(1 for s in st if s.senders) + 1)) * a.steps,
+                "messages_per_superstep": [s.messages_sent for s in st]}
+        print(json.dumps(line), flush=True)
+    h.destroy()
+
+
 def run_cc_batch(a, count=64):
     """Hashmin on 64 undirected R-MAT graphs (EF 16, uneven scales 10..20, seeds 1..64) held in
     one batch graph, one ipg_hashmin_cc_batch_dev call per step, against 64 separate graphs run
@@ -695,6 +804,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload in ("pagerank16", "hashmin20"):
+        run_small_config(a, a.workload)
     elif a.workload == "batch":
         run_batch(a)
     elif a.workload == "cc-batch":

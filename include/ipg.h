@@ -350,10 +350,11 @@ typedef struct {
  * under concurrent load other choices can be faster, so it is off by default. */
 #define IPG_SERVER_AUTOTUNE 1u
 /* ipg_server_create runs every program the server dispatches once on every graph
- * (one SSSP, one batched SSSP of 32 sources, one PageRank update, and Hashmin on
- * undirected graphs) into a scratch buffer, so that the graphs' device
- * workspaces exist before the first query instead of being allocated while
- * queries wait.  With a workspace budget, workers may release them later. */
+ * (one SSSP, one batched SSSP of 32 sources, PageRank with 10 updates, and
+ * Hashmin on undirected graphs) into a scratch buffer, so that the graphs' device
+ * workspaces and captured superstep loops exist before the first query instead
+ * of being made while queries wait.  With a workspace budget, workers may
+ * release them later. */
 #define IPG_SERVER_PREPARE 2u
 
 /* graphs: count graph handles (all on the same device); opt may be NULL. */

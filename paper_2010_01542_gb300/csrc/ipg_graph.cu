@@ -493,6 +493,8 @@ void release_workspace(ipg_graph* g) {
         if (p) cudaFree(p);
         p = nullptr;
     };
+    if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);  // it refers to the buffers below
+    g->pr_exec = nullptr;
     f(g->inv_outdeg);
     f(g->pr_box[0]);
     f(g->pr_box[1]);
@@ -559,6 +561,7 @@ static void free_graph(ipg_graph* g) {
     f(g->inst_base);
     f(g->inst_msgs);
     delete[] g->inst_base_host;
+    if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);
     batch_free(g);
     generic_free(g);
     if (g->h_counters) cudaFreeHost(g->h_counters);

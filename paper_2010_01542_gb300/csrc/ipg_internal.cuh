@@ -116,6 +116,8 @@ struct ipg_graph {
     uint64_t pr_tiles = 0;
     float* pr_out_stage = nullptr;          // host-variant output staging
     size_t pr_out_stage_cap = 0;
+    cudaGraphExec_t pr_exec = nullptr;      // captured superstep loop (ipg_pagerank.cu)
+    uint64_t pr_exec_key = 0;               // updates and launch shape it was captured for
 
     // push (Hashmin / SSSP) workspace
     uint32_t* stamp = nullptr;       // superstep in which the vertex was last appended to a frontier

@@ -266,6 +266,66 @@ static void pr_launch(const PrLaunch& L, ipg_graph* g, const float* in, float* o
 
 }  // namespace
 
+// Enqueues PageRank's `updates` supersteps (initial outbox, then pull + fix-up per
+// superstep) on st; the final ranks land in g->pr_rank.
+static ipg_status pr_enqueue_loop(ipg_graph* g, const PrLaunch& L, uint32_t updates, float base, float damp,
+                                  cudaStream_t st) {
+    const uint32_t n = g->n;
+    pr_init_kernel<<<grid_cap(n), 256, 0, st>>>(g->inv_outdeg, n, 1.0f / (float)n, g->pr_box[0]);
+    int cur = 0;
+    for (uint32_t t = 1; t <= updates; ++t) {
+        const bool fin = t == updates;
+        const float* in = g->pr_box[cur];
+        float* outb = g->pr_box[cur ^ 1];
+        if (fin)
+            pr_launch<true>(L, g, in, outb, st, base, damp);
+        else
+            pr_launch<false>(L, g, in, outb, st, base, damp);
+        const unsigned fg = grid_cap(g->pr_tiles);
+        if (fin)
+            pr_fixup_kernel<true><<<fg, 256, 0, st>>>(g->csc_off, g->pr_tile_row, g->pr_head, g->pr_tail,
+                                                      g->inv_outdeg, outb, g->pr_rank, g->pr_tiles, n, base, damp);
+        else
+            pr_fixup_kernel<false><<<fg, 256, 0, st>>>(g->csc_off, g->pr_tile_row, g->pr_head, g->pr_tail,
+                                                       g->inv_outdeg, outb, g->pr_rank, g->pr_tiles, n, base, damp);
+        cur ^= 1;
+    }
+    IPG_CUDA(cudaGetLastError());
+    return IPG_OK;
+}
+
+// Captures the superstep loop into g->pr_exec unless one for the same update
+// count and launch shape exists.  The graph refers to the graph's own buffers
+// only (never to a caller's), and is destroyed with them.
+ipg_status pr_loop_graph(ipg_graph* g, uint32_t updates, float base, float damp) {
+    PrLaunch L;
+    IPG_TRY(pr_launch_shape(g, &L));
+    const uint64_t key = ((uint64_t)updates << 32) ^ ((uint64_t)L.grid << 8) ^ ((uint64_t)L.threads << 1) ^
+                         (uint64_t)L.direct ^ ((uint64_t)(pr_carveout_for(g) + 1) << 20);
+    if (g->pr_exec && g->pr_exec_key == key) return IPG_OK;
+    if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);
+    g->pr_exec = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    IPG_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    ipg_status rc = IPG_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = pr_enqueue_loop(g, L, updates, base, damp, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+        if (rc == IPG_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g->pr_exec, graph, 0);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    if (rc != IPG_OK) return rc;
+    if (e != cudaSuccess) {
+        g->pr_exec = nullptr;
+        return cuda_fail(e, "PageRank superstep graph", __FILE__, __LINE__);
+    }
+    g->pr_exec_key = key;
+    return IPG_OK;
+}
+
 // events for per-superstep timing (per host thread)
 static thread_local cudaEvent_t* t_events = nullptr;
 static thread_local size_t t_events_cap = 0;
@@ -304,6 +364,12 @@ static ipg_status pagerank_run(ipg_graph* g, uint32_t updates, float* ranks_dev,
         if (timing) IPG_TRY(ensure_events(g, 3 * (size_t)updates + 1, &ev));
         if (updates == 0) {
             fill_kernel<<<grid_cap(n), 256, 0, st>>>(ranks_dev, n, 1.0f / N);
+            IPG_CUDA(cudaGetLastError());
+        } else if (!timing) {
+            // the whole superstep loop as one captured graph (built once per shape)
+            IPG_TRY(pr_loop_graph(g, updates, base, damp));
+            IPG_CUDA(cudaGraphLaunch(g->pr_exec, st));
+            unpermute_kernel<<<grid_cap(n), 256, 0, st>>>(g->pr_rank, g->inv, n, ranks_dev);
             IPG_CUDA(cudaGetLastError());
         } else {
             pr_init_kernel<<<grid_cap(n), 256, 0, st>>>(g->inv_outdeg, n, 1.0f / N, g->pr_box[0]);

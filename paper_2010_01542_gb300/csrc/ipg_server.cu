@@ -91,7 +91,8 @@ ipg_status prepare_graphs(ipg_graph* const* graphs, uint32_t count) {
         for (uint32_t k = 0; k < kSources; ++k) src[k] = (uint32_t)((uint64_t)g->n * k / kSources);
         r = ipg_sssp_dev(g, 0, scratch, nullptr, g->stream);
         if (r == IPG_OK) r = sssp_batch_run(g, src, kSources, scratch, nullptr, g->stream);
-        if (r == IPG_OK) r = ipg_pagerank_dev(g, 1, reinterpret_cast<float*>(scratch), nullptr, g->stream);
+        // PageRank with the paper's 10 updates: also captures that loop's graph
+        if (r == IPG_OK) r = ipg_pagerank_dev(g, 10, reinterpret_cast<float*>(scratch), nullptr, g->stream);
         if (r == IPG_OK && !g->directed) r = ipg_hashmin_cc_dev(g, scratch, nullptr, g->stream);
         // the host-output staging of ipg_sssp / ipg_hashmin_cc / ipg_pagerank
         size_t cap = g->val_stage ? (size_t)g->n * sizeof(uint32_t) : 0;
