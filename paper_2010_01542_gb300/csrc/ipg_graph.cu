@@ -114,22 +114,62 @@ __global__ void expand_sources_kernel(const uint64_t* __restrict__ off, uint32_t
     }
 }
 
-__global__ void csc_gather_kernel(const uint32_t* __restrict__ idx, uint64_t m, const uint32_t* __restrict__ src_of,
-                                  const uint8_t* __restrict__ w8, const uint32_t* __restrict__ w32,
-                                  uint32_t* __restrict__ csc_src, uint8_t* __restrict__ csc_w8,
-                                  uint32_t* __restrict__ csc_w32) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        const uint32_t e = idx[i];
-        csc_src[i] = src_of[e];
-        if (csc_w8) csc_w8[i] = w8[e];
-        if (csc_w32) csc_w32[i] = w32[e];
+// key of out-edge e of row u: (destination << 32) | u; rows are in source order,
+// so a stable sort on the destination bits leaves every in-edge list sorted by source
+__global__ void csc_keys_kernel(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col, uint32_t n,
+                                unsigned long long* __restrict__ keys) {
+    uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t lane = threadIdx.x & 31;
+    uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t u = warp; u < n; u += nwarps) {
+        uint64_t b = off[u], e = off[u + 1];
+        for (uint64_t p = b + lane; p < e; p += 32) keys[p] = ((unsigned long long)col[p] << 32) | u;
     }
 }
 
-__global__ void iota_kernel(uint32_t* __restrict__ a, uint64_t m) {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) a[i] = (uint32_t)i;
+// CSC offsets from the destinations of the sorted in-edges: entry i starts every
+// row after the previous entry's destination up to its own, and the last entry
+// also closes the rows after it (offset m).  dst(i) = key(i) >> shift.  A gap of
+// up to kGapDirect rows is written by its thread; a longer one goes to a list
+// that csc_gap_fill_kernel writes in parallel (at most n / kGapDirect + 1 gaps).
+constexpr uint64_t kGapDirect = 256;
+
+struct CscGap {
+    unsigned long long first, last, value;  // rows [first, last] start at entry `value`
+};
+
+__device__ __forceinline__ void csc_gap(uint64_t first, uint64_t last, uint64_t value, uint64_t* __restrict__ csc_off,
+                                        CscGap* __restrict__ gaps, unsigned int* __restrict__ ngaps) {
+    if (first > last) return;
+    if (last - first < kGapDirect) {
+        for (uint64_t r = first; r <= last; ++r) csc_off[r] = value;
+    } else {
+        gaps[atomicAdd(ngaps, 1u)] = CscGap{first, last, value};
+    }
+}
+
+template <typename K>
+__global__ void csc_offsets_kernel(const K* __restrict__ keys, int shift, uint64_t m, uint32_t n,
+                                   uint64_t* __restrict__ csc_off, uint32_t* __restrict__ src_out,
+                                   CscGap* __restrict__ gaps, unsigned int* __restrict__ ngaps) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const K k = keys[i];
+        const uint64_t v = (uint64_t)(k >> shift);
+        const uint64_t vp = i ? (uint64_t)(keys[i - 1] >> shift) + 1 : 0;
+        if (vp <= v) csc_gap(vp, v, i, csc_off, gaps, ngaps);
+        if (i == m - 1) csc_gap(v + 1, n, m, csc_off, gaps, ngaps);
+        if (src_out) src_out[i] = (uint32_t)k;  // 64-bit keys: the source in the low word
+    }
+}
+
+__global__ void csc_gap_fill_kernel(const CscGap* __restrict__ gaps, const unsigned int* __restrict__ ngaps,
+                                    uint64_t* __restrict__ csc_off) {
+    const unsigned int count = *ngaps;
+    for (unsigned int q = blockIdx.x; q < count; q += gridDim.x) {
+        const CscGap gp = gaps[q];
+        for (uint64_t r = gp.first + threadIdx.x; r <= gp.last; r += blockDim.x) csc_off[r] = gp.value;
+    }
 }
 
 __global__ void count_in_degree_kernel(const uint32_t* __restrict__ col, uint64_t m,
@@ -147,6 +187,12 @@ __global__ void count_nonempty_kernel(const uint64_t* __restrict__ off, uint32_t
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// In-edge copy (CSC) of a directed graph, built on the device: a stable radix
+// sort of the out-edges by destination.  Unweighted: (destination, source) pairs
+// of 32-bit words.  Weighted: 64-bit keys (destination << 32 | source), sorted on
+// the destination bits only, carrying the weight as the value, so sources and
+// weights come out in place without a gather.  The offsets follow from the sorted
+// destinations in the same pass that unpacks the sources.
 ipg_status ensure_csc(ipg_graph* g, cudaStream_t st) {
     if (g->csc_ready) return IPG_OK;
     if (!g->directed) {
@@ -162,13 +208,14 @@ ipg_status ensure_csc(ipg_graph* g, cudaStream_t st) {
     const uint32_t n = g->n;
     const uint64_t m = g->m;
     const int sms = device_sms(g->device);
-    unsigned long long* indeg = nullptr;
     uint32_t* src_in = nullptr;
     uint32_t* keys_out = nullptr;
-    uint32_t* idx_in = nullptr;
-    uint32_t* idx_out = nullptr;
+    unsigned long long* wkeys_in = nullptr;
+    unsigned long long* wkeys_out = nullptr;
     void* temp = nullptr;
-    size_t temp_bytes = 0, scan_bytes = 0;
+    size_t temp_bytes = 0;
+    CscGap* gaps = nullptr;
+    unsigned int* ngaps = nullptr;
     ipg_status rc = IPG_OK;
     cudaError_t e;
 #define CSC_CUDA(call)                                             \
@@ -185,62 +232,70 @@ ipg_status ensure_csc(ipg_graph* g, cudaStream_t st) {
         if (g->w8) CSC_CUDA(cudaMalloc(&g->csc_w8, m ? m : 1));
         if (g->w) CSC_CUDA(cudaMalloc(&g->csc_w, sizeof(uint32_t) * (m ? m : 1)));
         g->csc_owned = true;
-        CSC_CUDA(cudaMalloc(&indeg, sizeof(unsigned long long) * ((size_t)n + 1)));
-        CSC_CUDA(cudaMemsetAsync(indeg, 0, sizeof(unsigned long long) * ((size_t)n + 1), st));
-        if (m) {
-            count_in_degree_kernel<<<grid_for(m, sms, 16), 256, 0, st>>>(g->col, m, indeg);
-            CSC_CUDA(cudaGetLastError());
-        }
-        CSC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, indeg, (unsigned long long*)g->csc_off,
-                                               (long long)n + 1, st));
-        if (m) {
+        if (!m) {
+            CSC_CUDA(cudaMemsetAsync(g->csc_off, 0, sizeof(uint64_t) * ((size_t)n + 1), st));
+        } else {
             int bits = 1;
             while (bits < 32 && (1ull << bits) < (uint64_t)n) ++bits;
-            CSC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, (const uint32_t*)nullptr, (uint32_t*)nullptr,
-                                                     (const uint32_t*)nullptr, (uint32_t*)nullptr, (long long)m, 0,
-                                                     bits, st));
-        }
-        if (scan_bytes > temp_bytes) temp_bytes = scan_bytes;
-        CSC_CUDA(cudaMalloc(&temp, temp_bytes ? temp_bytes : 16));
-        CSC_CUDA(cub::DeviceScan::ExclusiveSum(temp, scan_bytes, indeg, (unsigned long long*)g->csc_off,
-                                               (long long)n + 1, st));
-        if (m) {
-            CSC_CUDA(cudaMalloc(&src_in, sizeof(uint32_t) * m));
-            CSC_CUDA(cudaMalloc(&keys_out, sizeof(uint32_t) * m));
-            expand_sources_kernel<<<grid_for((uint64_t)n * 32, sms, 16), 256, 0, st>>>(g->off, n, src_in);
-            CSC_CUDA(cudaGetLastError());
-            int bits = 1;
-            while (bits < 32 && (1ull << bits) < (uint64_t)n) ++bits;
-            size_t tb = temp_bytes;
+            const unsigned grid = grid_for(m, sms, 16);
+            const size_t max_gaps = (size_t)n / kGapDirect + 2;
+            CSC_CUDA(cudaMalloc(&gaps, sizeof(CscGap) * max_gaps));
+            CSC_CUDA(cudaMalloc(&ngaps, sizeof(unsigned int)));
+            CSC_CUDA(cudaMemsetAsync(ngaps, 0, sizeof(unsigned int), st));
             if (!weighted) {
-                CSC_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, (const uint32_t*)g->col, keys_out,
+                CSC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, (const uint32_t*)nullptr,
+                                                         (uint32_t*)nullptr, (const uint32_t*)nullptr,
+                                                         (uint32_t*)nullptr, (long long)m, 0, bits, st));
+                CSC_CUDA(cudaMalloc(&temp, temp_bytes ? temp_bytes : 16));
+                CSC_CUDA(cudaMalloc(&src_in, sizeof(uint32_t) * m));
+                CSC_CUDA(cudaMalloc(&keys_out, sizeof(uint32_t) * m));
+                expand_sources_kernel<<<grid_for((uint64_t)n * 32, sms, 16), 256, 0, st>>>(g->off, n, src_in);
+                CSC_CUDA(cudaGetLastError());
+                CSC_CUDA(cub::DeviceRadixSort::SortPairs(temp, temp_bytes, (const uint32_t*)g->col, keys_out,
                                                          (const uint32_t*)src_in, g->csc_src, (long long)m, 0, bits,
                                                          st));
+                csc_offsets_kernel<uint32_t><<<grid, 256, 0, st>>>(keys_out, 0, m, n, g->csc_off, nullptr, gaps,
+                                                                   ngaps);
             } else {
-                // sort edge indices by destination (stable), then gather sources and weights
-                CSC_CUDA(cudaMalloc(&idx_in, sizeof(uint32_t) * m));
-                CSC_CUDA(cudaMalloc(&idx_out, sizeof(uint32_t) * m));
-                iota_kernel<<<grid_for(m, sms, 16), 256, 0, st>>>(idx_in, m);
+                CSC_CUDA(cudaMalloc(&wkeys_in, sizeof(unsigned long long) * m));
+                CSC_CUDA(cudaMalloc(&wkeys_out, sizeof(unsigned long long) * m));
+                csc_keys_kernel<<<grid_for((uint64_t)n * 32, sms, 16), 256, 0, st>>>(g->off, g->col, n, wkeys_in);
                 CSC_CUDA(cudaGetLastError());
-                CSC_CUDA(cub::DeviceRadixSort::SortPairs(temp, tb, (const uint32_t*)g->col, keys_out,
-                                                         (const uint32_t*)idx_in, idx_out, (long long)m, 0, bits,
-                                                         st));
-                csc_gather_kernel<<<grid_for(m, sms, 16), 256, 0, st>>>(idx_out, m, src_in, g->w8, g->w, g->csc_src,
-                                                                        g->csc_w8, g->csc_w);
-                CSC_CUDA(cudaGetLastError());
+                if (g->w8) {
+                    CSC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, (const unsigned long long*)nullptr,
+                                                             (unsigned long long*)nullptr, (const uint8_t*)nullptr,
+                                                             (uint8_t*)nullptr, (long long)m, 32, 32 + bits, st));
+                    CSC_CUDA(cudaMalloc(&temp, temp_bytes ? temp_bytes : 16));
+                    CSC_CUDA(cub::DeviceRadixSort::SortPairs(temp, temp_bytes, (const unsigned long long*)wkeys_in,
+                                                             wkeys_out, (const uint8_t*)g->w8, g->csc_w8, (long long)m,
+                                                             32, 32 + bits, st));
+                } else {
+                    CSC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, (const unsigned long long*)nullptr,
+                                                             (unsigned long long*)nullptr, (const uint32_t*)nullptr,
+                                                             (uint32_t*)nullptr, (long long)m, 32, 32 + bits, st));
+                    CSC_CUDA(cudaMalloc(&temp, temp_bytes ? temp_bytes : 16));
+                    CSC_CUDA(cub::DeviceRadixSort::SortPairs(temp, temp_bytes, (const unsigned long long*)wkeys_in,
+                                                             wkeys_out, (const uint32_t*)g->w, g->csc_w, (long long)m,
+                                                             32, 32 + bits, st));
+                }
+                csc_offsets_kernel<unsigned long long><<<grid, 256, 0, st>>>(wkeys_out, 32, m, n, g->csc_off,
+                                                                              g->csc_src, gaps, ngaps);
             }
+            csc_gap_fill_kernel<<<(unsigned)sms * 4, 256, 0, st>>>(gaps, ngaps, g->csc_off);
+            CSC_CUDA(cudaGetLastError());
         }
         CSC_CUDA(cudaStreamSynchronize(st));
         g->csc_ready = true;
     }
 done:
 #undef CSC_CUDA
-    if (indeg) cudaFree(indeg);
     if (src_in) cudaFree(src_in);
     if (keys_out) cudaFree(keys_out);
-    if (idx_in) cudaFree(idx_in);
-    if (idx_out) cudaFree(idx_out);
+    if (wkeys_in) cudaFree(wkeys_in);
+    if (wkeys_out) cudaFree(wkeys_out);
     if (temp) cudaFree(temp);
+    if (gaps) cudaFree(gaps);
+    if (ngaps) cudaFree(ngaps);
     if (rc != IPG_OK) {
         if (g->csc_off) cudaFree(g->csc_off);
         if (g->csc_src) cudaFree(g->csc_src);
