@@ -561,9 +561,10 @@ def run_small_config(a, kind):
         tune = ipg.ipg_autotune(h, ipg.IPG_TUNE_PAGERANK if pr else ipg.IPG_TUNE_HASHMIN, stream=stream)
         tune = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in tune.items()}
 
-    # PageRank's timed steps run without per-superstep events, as one captured graph; a
-    # separate run with events gives the pull kernel's time for the roofline
-    def step(timing=not pr):
+    # the timed steps run without per-superstep events, so that the superstep loop runs
+    # as a captured CUDA graph; separate runs with events give the kernels' times for
+    # the roofline
+    def step(timing=False):
         flags = ipg.IPG_STAT_TIMING if timing else 0
         if pr:
             return ipg.ipg_pagerank_dev(h, PR_UPDATES, out, stats_flags=flags, stream=stream)
@@ -585,10 +586,11 @@ def run_small_config(a, kind):
     ms = e0.elapsed_time(e1)
     count, st = runs[-1]
     edges = PR_UPDATES * g.m if pr else sum(s.messages_sent for s in st)
+    assert all(c == count for c, _ in runs)
     rate, ms_max = replica_throughput(edges * a.steps, ms, world)
     # roofline of the step's dominant kernel (PageRank pull / pull-min or push relax)
     peak, peak_kind = peak_hbm()
-    timed_runs = runs if not pr else [step(timing=True) for _ in range(3)]
+    timed_runs = [step(timing=True) for _ in range(3)]
     recs = [s for _, sts in timed_runs for s in sts if s.flags & ipg.IPG_STAT_TIMING]
     if pr:
         byts = 8 * g.m + 24 * g.n

@@ -398,6 +398,11 @@ void ipg_server_destroy(ipg_server* s);
  *                   sources of a group) have fewer than m / batch_divisor out-edges
  *                   runs in push form, else in pull form.  0 = always pull.
  *                   Default 6.
+ *   "push_loop"     Hashmin/SSSP: 1 = the superstep loop runs on the device inside a
+ *                   CUDA graph (a conditional WHILE node; a few host synchronisations
+ *                   per run) whenever no per-superstep timing is asked for and the
+ *                   stats buffer holds at most 65536 records; 0 = the host drives
+ *                   every superstep.  Default 1.
  * Unknown names or invalid values return IPG_EINVAL.  Set knobs between calls,
  * not while a call runs.  A graph tuned by ipg_autotune uses its own values of
  * pull_divisor, batch_divisor, pr_engine and pr_carveout instead of these.

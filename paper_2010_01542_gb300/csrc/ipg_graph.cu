@@ -550,6 +550,10 @@ void release_workspace(ipg_graph* g) {
     };
     if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);  // it refers to the buffers below
     g->pr_exec = nullptr;
+    for (auto& x : g->push_exec) {  // so do the superstep loop graphs
+        if (x) cudaGraphExecDestroy(x);
+        x = nullptr;
+    }
     f(g->inv_outdeg);
     f(g->pr_box[0]);
     f(g->pr_box[1]);
@@ -617,6 +621,11 @@ static void free_graph(ipg_graph* g) {
     f(g->inst_msgs);
     delete[] g->inst_base_host;
     if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);
+    for (auto& x : g->push_exec)
+        if (x) cudaGraphExecDestroy(x);
+    f(g->loop);
+    f(g->loop_rec);
+    if (g->h_loop) cudaFreeHost(g->h_loop);
     batch_free(g);
     generic_free(g);
     if (g->h_counters) cudaFreeHost(g->h_counters);
@@ -855,6 +864,11 @@ ipg_status ipg_set_tuning(const char* name, int64_t value) {
         tuning().combine_warp = value;
         return IPG_OK;
     }
+    if (!strcmp(name, "push_loop")) {
+        if (value != 0 && value != 1) return set_error(IPG_EINVAL, "ipg_set_tuning: push_loop must be 0 or 1");
+        tuning().push_loop = value;
+        return IPG_OK;
+    }
     if (!strcmp(name, "batch_divisor")) {
         if (value < 0) return set_error(IPG_EINVAL, "ipg_set_tuning: batch_divisor must be >= 0");
         tuning().batch_divisor = value;
@@ -886,6 +900,10 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value) {
     }
     if (!strcmp(name, "combine_warp")) {
         *value = tuning().combine_warp;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "push_loop")) {
+        *value = tuning().push_loop;
         return IPG_OK;
     }
     if (!strcmp(name, "batch_divisor")) {

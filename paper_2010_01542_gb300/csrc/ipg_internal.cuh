@@ -26,6 +26,34 @@ struct PushCounters {
     unsigned int pad[9];
 };
 
+// Device-resident state of a Hashmin/SSSP superstep loop run inside a CUDA graph
+// (ipg_push.cu): the kernels read the frontier from it, so their launch
+// parameters never change, and the step kernel advances it.
+struct PushLoop {
+    unsigned int cur;      // frontier buffer holding the senders
+    unsigned int f;        // senders
+    unsigned int s;        // Pregel superstep number
+    unsigned int pull;     // 1: this superstep runs in pull form
+    unsigned int iter;     // supersteps run by the current graph launch
+    unsigned int done;     // 1: no superstep left
+    unsigned int count;    // superstep count once done
+    unsigned int nrec;     // stats records written
+    unsigned int status;   // kStatus* bits
+    unsigned int pad;
+    unsigned long long divisor;         // pull when messages * divisor >= m (0: never)
+    unsigned long long prev_receivers;  // receivers of the previous superstep (stats mode)
+};
+
+// frontier of a loop-driven superstep (loop != NULL) or of a host-driven one
+__device__ __forceinline__ const uint32_t* loop_frontier(const uint32_t* F0, const uint32_t* F1,
+                                                         const PushLoop* loop) {
+    return loop && loop->cur ? F1 : F0;
+}
+__device__ __forceinline__ uint32_t* loop_next(uint32_t* N0, uint32_t* N1, const PushLoop* loop) {
+    return loop && loop->cur ? N0 : N1;
+}
+__device__ __forceinline__ uint32_t loop_f(uint32_t f, const PushLoop* loop) { return loop ? loop->f : f; }
+
 ipg_status set_error(ipg_status s, const char* fmt, ...);
 ipg_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
 
@@ -137,6 +165,11 @@ struct ipg_graph {
     ipg::PushCounters* counters = nullptr;    // device
     ipg::PushCounters* h_counters = nullptr;  // pinned host mirror
 
+    ipg::PushLoop* loop = nullptr;            // device loop state (graph-driven runs)
+    ipg_superstep_stats* loop_rec = nullptr;  // device stats records of a graph-driven run
+    ipg::PushLoop* h_loop = nullptr;          // pinned mirror
+    cudaGraphExec_t push_exec[8] = {};        // loop graphs: kind x receivers x weight kind (ipg_push.cu)
+
     void* batch = nullptr;          // batched-SSSP workspace (ipg_batch.cu)
     void* generic = nullptr;        // general-combiner workspace (ipg_generic.cu)
 
@@ -179,6 +212,10 @@ ipg_status map_to_internal(ipg_graph* g, uint32_t* ids, uint32_t k, cudaStream_t
 // in ipg_pull_min.cu
 ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, const uint32_t* F, const uint32_t* fval, uint32_t f,
                               uint32_t* val, uint32_t* next, cudaStream_t st, cudaEvent_t ev_kernel);
+// the pull form of a loop-driven superstep: every kernel returns at once unless
+// loop->pull is set; frontiers and sizes come from the loop block
+ipg_status pull_min_enqueue_loop(ipg_graph* g, bool sssp, bool recv, uint32_t* val, cudaStream_t st);
+ipg_status pull_min_prepare(ipg_graph* g, cudaStream_t st);
 // process-wide tuning knobs (ipg_set_tuning)
 struct Tuning {
     long long pull_divisor = 6;  // pull when a superstep's messages reach m / pull_divisor; 0 = never
@@ -186,6 +223,7 @@ struct Tuning {
     long long pr_threads = 256;  // PageRank pull kernel: threads per CTA (256 or 512)
     long long pr_carveout = -1;  // PageRank pull kernel: shared-memory carveout percent (-1 = smallest)
     long long batch_divisor = 6; // batched SSSP: push when the senders' out-edges < m / batch_divisor (0 = pull)
+    long long push_loop = 1;     // Hashmin/SSSP: 1 = superstep loop in a CUDA graph where possible, 0 = host loop
     long long pr_engine = 0;     // PageRank pull kernel: 0 staged messages, 1 direct (registers)
 };
 Tuning& tuning();

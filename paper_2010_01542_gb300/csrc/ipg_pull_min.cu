@@ -21,8 +21,20 @@ namespace {
 constexpr int kPmThreads = 256;
 constexpr int kPmItems = 8;
 
-__global__ void sval_scatter_kernel(const uint32_t* __restrict__ F, const uint32_t* __restrict__ fval, uint32_t f,
-                                    uint32_t* __restrict__ sval) {
+// loop-driven supersteps (loop != NULL) return at once unless they run in pull form
+__device__ __forceinline__ bool pull_skip(const PushLoop* loop) { return loop && !loop->pull; }
+
+__global__ void sval_fill_kernel(uint32_t* __restrict__ sval, uint32_t n, const PushLoop* __restrict__ loop) {
+    if (pull_skip(loop)) return;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) sval[i] = kInf;
+}
+
+__global__ void sval_scatter_kernel(const uint32_t* F0, const uint32_t* F1, const uint32_t* __restrict__ fval,
+                                    uint32_t f, const PushLoop* __restrict__ loop, uint32_t* __restrict__ sval) {
+    if (pull_skip(loop)) return;
+    const uint32_t* __restrict__ F = loop_frontier(F0, F1, loop);
+    f = loop_f(f, loop);
     uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < f; i += stride) sval[F[i]] = fval[i];
 }
@@ -100,7 +112,10 @@ __global__ void __launch_bounds__(kPmThreads) pull_min_kernel(
     const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ csc_src, const uint8_t* __restrict__ csc_w8,
     const uint32_t* __restrict__ csc_w32, const uint32_t* __restrict__ sval, uint32_t* __restrict__ val,
     const uint32_t* __restrict__ tile_row, uint32_t* __restrict__ tile_head, uint32_t* __restrict__ tile_tail,
-    uint64_t tiles, uint32_t n, uint64_t m, uint32_t* __restrict__ next, PushCounters* __restrict__ ctr) {
+    uint64_t tiles, uint32_t n, uint64_t m, uint32_t* next0, uint32_t* next1, const PushLoop* __restrict__ loop,
+    PushCounters* __restrict__ ctr) {
+    if (pull_skip(loop)) return;
+    uint32_t* __restrict__ next = loop_next(next0, next1, loop);
     __shared__ MpShared<kPmThreads, kPmItems, uint32_t> sh;
     __shared__ uint32_t s_q[kPmQueue];
     __shared__ unsigned int s_qn, s_recv, s_base;
@@ -132,8 +147,11 @@ __global__ void __launch_bounds__(kPmThreads) pull_min_kernel(
 template <bool kRecv>
 __global__ void pull_min_fixup_kernel(const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ tile_row,
                                       const uint32_t* __restrict__ tile_head, const uint32_t* __restrict__ tile_tail,
-                                      uint32_t* __restrict__ val, uint64_t tiles, uint32_t n,
-                                      uint32_t* __restrict__ next, PushCounters* __restrict__ ctr) {
+                                      uint32_t* __restrict__ val, uint64_t tiles, uint32_t n, uint32_t* next0,
+                                      uint32_t* next1, const PushLoop* __restrict__ loop,
+                                      PushCounters* __restrict__ ctr) {
+    if (pull_skip(loop)) return;
+    uint32_t* __restrict__ next = loop_next(next0, next1, loop);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += stride) {
         uint32_t row;
@@ -151,21 +169,31 @@ __global__ void pull_min_fixup_kernel(const uint64_t* __restrict__ csc_off, cons
 }
 
 template <bool kAddWeight, int kWeightKind, bool kRecv>
-ipg_status launch(ipg_graph* g, uint32_t* val, uint32_t* next, cudaStream_t st) {
+ipg_status launch(ipg_graph* g, uint32_t* val, uint32_t* next0, uint32_t* next1, const PushLoop* loop,
+                  cudaStream_t st) {
     const void* k = reinterpret_cast<const void*>(&pull_min_kernel<kAddWeight, kWeightKind, kRecv>);
     unsigned grid = 1;
     IPG_TRY(pull_grid(&k, 1, kPmThreads, g->device, g->pr_tiles, (int)pr_carveout_for(g), &grid));
     pull_min_kernel<kAddWeight, kWeightKind, kRecv><<<grid, kPmThreads, 0, st>>>(
         g->csc_off, g->csc_src, g->csc_w8, g->csc_w, g->sval, val, g->pr_tile_row, (uint32_t*)g->pr_head,
-        (uint32_t*)g->pr_tail, g->pr_tiles, g->n, g->m, next, g->counters);
+        (uint32_t*)g->pr_tail, g->pr_tiles, g->n, g->m, next0, next1, loop, g->counters);
     IPG_CUDA(cudaGetLastError());
     return IPG_OK;
 }
 
 template <bool kAddWeight, int kWeightKind>
-ipg_status launch2(bool recv, ipg_graph* g, uint32_t* val, uint32_t* next, cudaStream_t st) {
-    return recv ? launch<kAddWeight, kWeightKind, true>(g, val, next, st)
-                : launch<kAddWeight, kWeightKind, false>(g, val, next, st);
+ipg_status launch2(bool recv, ipg_graph* g, uint32_t* val, uint32_t* next0, uint32_t* next1, const PushLoop* loop,
+                   cudaStream_t st) {
+    return recv ? launch<kAddWeight, kWeightKind, true>(g, val, next0, next1, loop, st)
+                : launch<kAddWeight, kWeightKind, false>(g, val, next0, next1, loop, st);
+}
+
+ipg_status launch_any(ipg_graph* g, bool sssp, bool recv, uint32_t* val, uint32_t* next0, uint32_t* next1,
+                      const PushLoop* loop, cudaStream_t st) {
+    if (!sssp) return launch2<false, 0>(recv, g, val, next0, next1, loop, st);
+    if (g->csc_w8) return launch2<true, 1>(recv, g, val, next0, next1, loop, st);
+    if (g->csc_w) return launch2<true, 2>(recv, g, val, next0, next1, loop, st);
+    return launch2<true, 0>(recv, g, val, next0, next1, loop, st);
 }
 
 unsigned small_grid(uint64_t work) {
@@ -173,6 +201,19 @@ unsigned small_grid(uint64_t work) {
     if (b < 1) b = 1;
     return (unsigned)(b < 152 * 16 ? b : 152 * 16);
 }
+
+void launch_fixup(ipg_graph* g, bool recv, uint32_t* val, uint32_t* next0, uint32_t* next1, const PushLoop* loop,
+                  cudaStream_t st) {
+    if (recv)
+        pull_min_fixup_kernel<true><<<small_grid(g->pr_tiles), 256, 0, st>>>(
+            g->csc_off, g->pr_tile_row, (const uint32_t*)g->pr_head, (const uint32_t*)g->pr_tail, val, g->pr_tiles,
+            g->n, next0, next1, loop, g->counters);
+    else
+        pull_min_fixup_kernel<false><<<small_grid(g->pr_tiles), 256, 0, st>>>(
+            g->csc_off, g->pr_tile_row, (const uint32_t*)g->pr_head, (const uint32_t*)g->pr_tail, val, g->pr_tiles,
+            g->n, next0, next1, loop, g->counters);
+}
+
 
 }  // namespace
 
@@ -188,25 +229,23 @@ ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, const uint32_t
                               uint32_t* val, uint32_t* next, cudaStream_t st, cudaEvent_t ev_kernel) {
     IPG_TRY(pull_min_prepare(g, st));
     IPG_CUDA(cudaMemsetAsync(g->sval, 0xFF, sizeof(uint32_t) * g->n, st));
-    sval_scatter_kernel<<<small_grid(f), 256, 0, st>>>(F, fval, f, g->sval);
+    sval_scatter_kernel<<<small_grid(f), 256, 0, st>>>(F, F, fval, f, nullptr, g->sval);
     IPG_CUDA(cudaGetLastError());
     if (ev_kernel) IPG_CUDA(cudaEventRecord(ev_kernel, st));
-    if (!sssp)
-        IPG_TRY((launch2<false, 0>(recv, g, val, next, st)));
-    else if (g->csc_w8)
-        IPG_TRY((launch2<true, 1>(recv, g, val, next, st)));
-    else if (g->csc_w)
-        IPG_TRY((launch2<true, 2>(recv, g, val, next, st)));
-    else
-        IPG_TRY((launch2<true, 0>(recv, g, val, next, st)));
-    if (recv)
-        pull_min_fixup_kernel<true><<<small_grid(g->pr_tiles), 256, 0, st>>>(
-            g->csc_off, g->pr_tile_row, (const uint32_t*)g->pr_head, (const uint32_t*)g->pr_tail, val, g->pr_tiles,
-            g->n, next, g->counters);
-    else
-        pull_min_fixup_kernel<false><<<small_grid(g->pr_tiles), 256, 0, st>>>(
-            g->csc_off, g->pr_tile_row, (const uint32_t*)g->pr_head, (const uint32_t*)g->pr_tail, val, g->pr_tiles,
-            g->n, next, g->counters);
+    IPG_TRY(launch_any(g, sssp, recv, val, next, next, nullptr, st));
+    launch_fixup(g, recv, val, next, next, nullptr, st);
+    IPG_CUDA(cudaGetLastError());
+    return IPG_OK;
+}
+
+// the same superstep with sizes and frontiers read from g->loop (graph capture)
+ipg_status pull_min_enqueue_loop(ipg_graph* g, bool sssp, bool recv, uint32_t* val, cudaStream_t st) {
+    const unsigned fixed = (unsigned)sm_count_of(g->device) * 8;
+    sval_fill_kernel<<<fixed, 256, 0, st>>>(g->sval, g->n, g->loop);
+    sval_scatter_kernel<<<fixed, 256, 0, st>>>(g->frontier[0], g->frontier[1], g->fr_val, 0, g->loop, g->sval);
+    IPG_CUDA(cudaGetLastError());
+    IPG_TRY(launch_any(g, sssp, recv, val, g->frontier[0], g->frontier[1], g->loop, st));
+    launch_fixup(g, recv, val, g->frontier[0], g->frontier[1], g->loop, st);
     IPG_CUDA(cudaGetLastError());
     return IPG_OK;
 }

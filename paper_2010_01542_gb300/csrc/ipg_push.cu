@@ -26,6 +26,7 @@
 // during superstep s is sent only in s+1: the run is the synchronous Pregel
 // execution, superstep for superstep, and the per-superstep counts match the
 // model exactly.
+#include <algorithm>
 #include <vector>
 
 #include "ipg_internal.cuh"
@@ -99,31 +100,46 @@ __global__ void sssp_init_kernel(uint32_t* __restrict__ val, uint32_t* __restric
     if (blockIdx.x == 0 && threadIdx.x == 0) frontier[0] = s;
 }
 
+// The frontier passes take the frontier from the loop block when one is given
+// (loop-driven supersteps in a CUDA graph), else from their arguments, and walk
+// the frontier's blocks of kFrBlock entries grid-stride.
+
 // pass 1 of the frontier prefix: one degree total per block of 2048 entries
-__global__ void __launch_bounds__(kFrThreads) fr_reduce_kernel(const uint32_t* __restrict__ F, uint32_t f,
+__global__ void __launch_bounds__(kFrThreads) fr_reduce_kernel(const uint32_t* F0, const uint32_t* F1, uint32_t f,
+                                                               const PushLoop* __restrict__ loop,
                                                                const uint64_t* __restrict__ off,
                                                                unsigned long long* __restrict__ block_sums) {
     __shared__ unsigned long long s_tmp[33];
-    const uint64_t b0 = (uint64_t)blockIdx.x * kFrBlock;
-    unsigned long long d = 0;
+    const uint32_t* __restrict__ F = loop_frontier(F0, F1, loop);
+    f = loop_f(f, loop);
+    const uint32_t nb = (f + kFrBlock - 1) / kFrBlock;
+    for (uint32_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        const uint64_t b0 = (uint64_t)blk * kFrBlock;
+        unsigned long long d = 0;
 #pragma unroll
-    for (int q = 0; q < kFrItems; ++q) {
-        uint64_t i = b0 + (uint64_t)q * kFrThreads + threadIdx.x;
-        if (i < f) {
-            uint32_t u = F[i];
-            d += off[u + 1] - off[u];
+        for (int q = 0; q < kFrItems; ++q) {
+            uint64_t i = b0 + (uint64_t)q * kFrThreads + threadIdx.x;
+            if (i < f) {
+                uint32_t u = F[i];
+                d += off[u + 1] - off[u];
+            }
         }
+        unsigned long long t = block_sum_u64(d, s_tmp);
+        if (threadIdx.x == 0) block_sums[blk] = t;
+        __syncthreads();  // s_tmp is reused by the next block
     }
-    unsigned long long t = block_sum_u64(d, s_tmp);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = t;
 }
 
-// single CTA: exclusive scan of the block totals, edge count and tile count
+// single CTA: exclusive scan of the block totals, edge count and tile count; a
+// loop-driven superstep also picks its form here (pull when its messages reach
+// m / divisor)
 __global__ void __launch_bounds__(kScanThreads) fr_scan_kernel(unsigned long long* __restrict__ block_sums,
-                                                               uint32_t nb, uint32_t f,
-                                                               unsigned long long* __restrict__ prefix,
+                                                               uint32_t nb, uint32_t f, PushLoop* __restrict__ loop,
+                                                               uint64_t m, unsigned long long* __restrict__ prefix,
                                                                PushCounters* __restrict__ ctr) {
     __shared__ unsigned long long s_tmp[33];
+    f = loop_f(f, loop);
+    if (loop) nb = (f + kFrBlock - 1) / kFrBlock;
     const uint32_t per = (nb + kScanThreads - 1) / kScanThreads;
     const uint64_t a = (uint64_t)threadIdx.x * per;
     const uint64_t b = a + per < nb ? a + per : nb;
@@ -142,16 +158,18 @@ __global__ void __launch_bounds__(kScanThreads) fr_scan_kernel(unsigned long lon
         ctr->tiles = (unsigned)(((unsigned long long)f + total + kPushTile - 1) / kPushTile);
         ctr->next_size = 0;
         ctr->receivers = 0;
+        if (loop)
+            loop->pull = loop->divisor > 0 && total > 0 && (double)total * (double)loop->divisor >= (double)m;
     }
 }
 
-// pass 2: per-entry exclusive prefix, row start and value snapshot
-__global__ void __launch_bounds__(kFrThreads) fr_write_kernel(
-    const uint32_t* __restrict__ F, uint32_t f, const uint64_t* __restrict__ off, const uint32_t* __restrict__ val,
-    const unsigned long long* __restrict__ block_off, unsigned long long* __restrict__ prefix,
-    unsigned long long* __restrict__ rowstart, uint32_t* __restrict__ fval) {
-    __shared__ unsigned long long s_tmp[33];
-    const uint64_t i0 = (uint64_t)blockIdx.x * kFrBlock + (uint64_t)threadIdx.x * kFrItems;
+__device__ __forceinline__ void fr_write_block(const uint32_t* __restrict__ F, uint32_t f, uint32_t blk,
+                                               const uint64_t* __restrict__ off, const uint32_t* __restrict__ val,
+                                               const unsigned long long* __restrict__ block_off,
+                                               unsigned long long* __restrict__ prefix,
+                                               unsigned long long* __restrict__ rowstart, uint32_t* __restrict__ fval,
+                                               unsigned long long* s_tmp) {
+    const uint64_t i0 = (uint64_t)blk * kFrBlock + (uint64_t)threadIdx.x * kFrItems;
     uint64_t st[kFrItems];
     unsigned long long deg[kFrItems];
     unsigned long long local = 0;
@@ -169,7 +187,7 @@ __global__ void __launch_bounds__(kFrThreads) fr_write_kernel(
         local += deg[q];
     }
     unsigned long long total;
-    unsigned long long run = block_exscan_u64(local, s_tmp, &total) + block_off[blockIdx.x];
+    unsigned long long run = block_exscan_u64(local, s_tmp, &total) + block_off[blk];
 #pragma unroll
     for (int q = 0; q < kFrItems; ++q) {
         uint64_t i = i0 + q;
@@ -180,6 +198,23 @@ __global__ void __launch_bounds__(kFrThreads) fr_write_kernel(
         run += deg[q];
     }
 }
+
+// pass 2: per-entry exclusive prefix, row start and value snapshot
+__global__ void __launch_bounds__(kFrThreads) fr_write_kernel(
+    const uint32_t* F0, const uint32_t* F1, uint32_t f, const PushLoop* __restrict__ loop,
+    const uint64_t* __restrict__ off, const uint32_t* __restrict__ val,
+    const unsigned long long* __restrict__ block_off, unsigned long long* __restrict__ prefix,
+    unsigned long long* __restrict__ rowstart, uint32_t* __restrict__ fval) {
+    __shared__ unsigned long long s_tmp[33];
+    const uint32_t* __restrict__ F = loop_frontier(F0, F1, loop);
+    f = loop_f(f, loop);
+    const uint32_t nb = (f + kFrBlock - 1) / kFrBlock;
+    for (uint32_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        fr_write_block(F, f, blk, off, val, block_off, prefix, rowstart, fval, s_tmp);
+        __syncthreads();  // s_tmp is reused by the next block
+    }
+}
+
 
 __device__ __forceinline__ uint32_t merge_path_rows(const unsigned long long* __restrict__ row_end, uint32_t nrows,
                                                     uint64_t nedges, uint64_t diag) {
@@ -196,7 +231,10 @@ __device__ __forceinline__ uint32_t merge_path_rows(const unsigned long long* __
 }
 
 __global__ void push_partition_kernel(const unsigned long long* __restrict__ prefix, uint32_t f,
-                                      const PushCounters* __restrict__ ctr, uint32_t* __restrict__ tile_row) {
+                                      const PushLoop* __restrict__ loop, const PushCounters* __restrict__ ctr,
+                                      uint32_t* __restrict__ tile_row) {
+    if (loop && loop->pull) return;
+    f = loop_f(f, loop);
     const uint64_t E = ctr->edges;
     const uint64_t tiles = ctr->tiles;
     const uint64_t total = (uint64_t)f + E;
@@ -224,8 +262,12 @@ __global__ void __launch_bounds__(kPushThreads) push_relax_kernel(
     const unsigned long long* __restrict__ prefix, const unsigned long long* __restrict__ rowstart,
     const uint32_t* __restrict__ fval, const uint32_t* __restrict__ tile_row, const uint32_t* __restrict__ col,
     const uint8_t* __restrict__ w8, const uint32_t* __restrict__ w32, uint32_t* __restrict__ val,
-    uint32_t* __restrict__ stamp, uint32_t* __restrict__ rstamp, uint32_t* __restrict__ next,
-    PushCounters* __restrict__ ctr, uint32_t f, uint32_t tag) {
+    uint32_t* __restrict__ stamp, uint32_t* __restrict__ rstamp, uint32_t* next0, uint32_t* next1,
+    const PushLoop* __restrict__ loop, PushCounters* __restrict__ ctr, uint32_t f, uint32_t tag) {
+    if (loop && loop->pull) return;
+    uint32_t* __restrict__ next = loop_next(next0, next1, loop);
+    f = loop_f(f, loop);
+    if (loop) tag = loop->s + 1;
     __shared__ uint32_t s_start[kPushTile + 1];
     __shared__ unsigned long long s_base[kPushTile + 1];
     __shared__ uint32_t s_val[kPushTile + 1];
@@ -378,33 +420,106 @@ int sm_count(int dev) {
     return v;
 }
 
+// next0 / next1: the next frontier of a host-driven superstep (both the same), or
+// the two frontier buffers of a loop-driven one, picked by loop->cur
 template <int kKind, int kWeightKind, bool kRecv>
-void launch_relax(unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next, uint32_t f,
-                  uint32_t tag) {
+void launch_relax(unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next0, uint32_t* next1,
+                  const PushLoop* loop, uint32_t f, uint32_t tag) {
     push_relax_kernel<kKind, kWeightKind, kRecv><<<grid, kPushThreads, 0, st>>>(
-        g->fr_prefix, g->fr_rowstart, g->fr_val, g->push_tile_row, g->col, g->w8, g->w, val, g->stamp, g->rstamp, next,
-        g->counters, f, tag);
+        g->fr_prefix, g->fr_rowstart, g->fr_val, g->push_tile_row, g->col, g->w8, g->w, val, g->stamp, g->rstamp,
+        next0, next1, loop, g->counters, f, tag);
 }
 
 template <int kKind, int kWeightKind>
-void launch_relax2(bool recv, unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next,
-                   uint32_t f, uint32_t tag) {
+void launch_relax2(bool recv, unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next0,
+                   uint32_t* next1, const PushLoop* loop, uint32_t f, uint32_t tag) {
     if (recv)
-        launch_relax<kKind, kWeightKind, true>(grid, st, g, val, next, f, tag);
+        launch_relax<kKind, kWeightKind, true>(grid, st, g, val, next0, next1, loop, f, tag);
     else
-        launch_relax<kKind, kWeightKind, false>(grid, st, g, val, next, f, tag);
+        launch_relax<kKind, kWeightKind, false>(grid, st, g, val, next0, next1, loop, f, tag);
 }
 
-void relax_dispatch(int kind, bool recv, unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next,
-                    uint32_t f, uint32_t tag) {
+void relax_dispatch(int kind, bool recv, unsigned grid, cudaStream_t st, ipg_graph* g, uint32_t* val, uint32_t* next0,
+                    uint32_t* next1, const PushLoop* loop, uint32_t f, uint32_t tag) {
     if (kind == kHashmin)
-        launch_relax2<kHashmin, 0>(recv, grid, st, g, val, next, f, tag);
+        launch_relax2<kHashmin, 0>(recv, grid, st, g, val, next0, next1, loop, f, tag);
     else if (g->w8)
-        launch_relax2<kSssp, 1>(recv, grid, st, g, val, next, f, tag);
+        launch_relax2<kSssp, 1>(recv, grid, st, g, val, next0, next1, loop, f, tag);
     else if (g->w)
-        launch_relax2<kSssp, 2>(recv, grid, st, g, val, next, f, tag);
+        launch_relax2<kSssp, 2>(recv, grid, st, g, val, next0, next1, loop, f, tag);
     else
-        launch_relax2<kSssp, 0>(recv, grid, st, g, val, next, f, tag);
+        launch_relax2<kSssp, 0>(recv, grid, st, g, val, next0, next1, loop, f, tag);
+}
+
+// ---------------------------------------------------------------------------
+// Loop-driven runs: the superstep loop inside a CUDA graph (conditional WHILE)
+
+constexpr unsigned kLoopCap = 64;          // supersteps per graph launch
+constexpr uint32_t kLoopRecords = 1 << 16; // stats records a loop-driven run keeps
+
+__global__ void loop_init_kernel(PushLoop* __restrict__ loop, uint32_t f, unsigned long long divisor) {
+    loop->cur = 0;
+    loop->f = f;
+    loop->s = 0;
+    loop->pull = 0;
+    loop->iter = 0;
+    loop->done = f == 0;
+    loop->count = 0;
+    loop->nrec = 0;
+    loop->status = 0;
+    loop->divisor = divisor;
+    loop->prev_receivers = 0;
+}
+
+__device__ __forceinline__ void loop_record(PushLoop* loop, ipg_superstep_stats* rec, const ipg_superstep_stats& r) {
+    if (loop->nrec < kLoopRecords) rec[loop->nrec] = r;
+    ++loop->nrec;
+}
+
+// End of a loop-driven superstep: the stats record, termination (no next
+// frontier: the receivers still run one more superstep if messages were sent),
+// then the next frontier becomes current and the WHILE condition is set.
+__global__ void loop_step_kernel(PushLoop* __restrict__ loop, PushCounters* __restrict__ ctr,
+                                 ipg_superstep_stats* __restrict__ rec, uint32_t n, int recv,
+                                 cudaGraphConditionalHandle handle) {
+    const unsigned long long edges = ctr->edges, receivers = ctr->receivers;
+    const uint32_t fn = ctr->next_size, s = loop->s;
+    uint32_t status = loop->status | ctr->status;
+    if (fn > n) status |= kStatusInternal;
+    ipg_superstep_stats r{};
+    r.superstep = s;
+    r.flags = (recv ? IPG_STAT_RECEIVERS : 0u) | (loop->pull ? IPG_STAT_PULL : 0u);
+    r.active = s == 0 ? n : (recv ? loop->prev_receivers : 0);
+    r.senders = loop->f;
+    r.messages_sent = edges;
+    r.receivers = recv ? receivers : 0;
+    loop_record(loop, rec, r);
+    bool more = false;
+    if (status) {
+        loop->done = 1;
+    } else if (fn == 0) {
+        loop->count = s + 1;
+        if (edges > 0) {  // the receivers run one more superstep, change nothing, send nothing
+            ipg_superstep_stats t{};
+            t.superstep = s + 1;
+            t.flags = recv ? IPG_STAT_RECEIVERS : 0u;
+            t.active = recv ? receivers : 0;
+            loop_record(loop, rec, t);
+            loop->count = s + 2;
+        }
+        loop->done = 1;
+    } else {
+        loop->prev_receivers = receivers;
+        loop->f = fn;
+        loop->cur ^= 1u;
+        loop->s = s + 1;
+        more = true;
+    }
+    loop->status = status;
+    const unsigned it = loop->iter + 1;
+    const bool again = more && it < kLoopCap;
+    loop->iter = again ? it : 0u;
+    cudaGraphSetConditional(handle, again ? 1u : 0u);
 }
 
 __global__ void unpermute_u32_kernel(const uint32_t* __restrict__ in, const uint32_t* __restrict__ inv, uint32_t n,
@@ -425,6 +540,119 @@ ipg_status ensure_events_push(size_t count, cudaEvent_t** evs) {
         cap = count;
     }
     *evs = ev;
+    return IPG_OK;
+}
+
+// loop-graph slot: program x receivers counting x pull form allowed
+int loop_slot(int kind, bool recv, bool pull) { return (kind == kSssp ? 4 : 0) + (recv ? 2 : 0) + (pull ? 1 : 0); }
+
+ipg_status ensure_loop_workspace(ipg_graph* g) {
+    if (g->loop) return IPG_OK;
+    IPG_CUDA(cudaMalloc(&g->loop_rec, sizeof(ipg_superstep_stats) * kLoopRecords));
+    IPG_CUDA(cudaHostAlloc(&g->h_loop, sizeof(PushLoop), cudaHostAllocDefault));
+    IPG_CUDA(cudaMalloc(&g->loop, sizeof(PushLoop)));
+    return IPG_OK;
+}
+
+// Builds [WHILE (cond) { superstep }] for one slot.  The body enqueues both forms
+// of the superstep; each returns at once unless fr_scan_kernel picked it.
+ipg_status push_loop_graph(ipg_graph* g, int kind, bool recv, bool pull, cudaGraphExec_t* out) {
+    const int sms = sm_count(g->device);
+    const unsigned fixed = (unsigned)sms * 8;
+    cudaGraph_t graph = nullptr;
+    cudaStream_t cap = nullptr;
+    ipg_status rc = IPG_OK;
+    do {
+        cudaError_t e = cudaGraphCreate(&graph, 0);
+        cudaGraphConditionalHandle handle;
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = handle;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(cap, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "superstep loop graph", __FILE__, __LINE__);
+            break;
+        }
+        fr_reduce_kernel<<<fixed, kFrThreads, 0, cap>>>(g->frontier[0], g->frontier[1], 0, g->loop, g->off,
+                                                        g->block_sums);
+        fr_scan_kernel<<<1, kScanThreads, 0, cap>>>(g->block_sums, 0, 0, g->loop, g->m, g->fr_prefix, g->counters);
+        fr_write_kernel<<<fixed, kFrThreads, 0, cap>>>(g->frontier[0], g->frontier[1], 0, g->loop, g->off, g->val,
+                                                       g->block_sums, g->fr_prefix, g->fr_rowstart, g->fr_val);
+        push_partition_kernel<<<(unsigned)sms * 2, 256, 0, cap>>>(g->fr_prefix, 0, g->loop, g->counters,
+                                                                 g->push_tile_row);
+        relax_dispatch(kind, recv, (unsigned)sms * 6, cap, g, g->val, g->frontier[0], g->frontier[1], g->loop, 0, 0);
+        if (pull) rc = pull_min_enqueue_loop(g, kind == kSssp, recv, g->val, cap);
+        loop_step_kernel<<<1, 1, 0, cap>>>(g->loop, g->counters, g->loop_rec, g->n, recv ? 1 : 0, handle);
+        cudaGraph_t body = nullptr;
+        e = cudaStreamEndCapture(cap, &body);
+        if (rc != IPG_OK) break;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "superstep loop graph capture", __FILE__, __LINE__);
+    } while (false);
+    if (cap) cudaStreamDestroy(cap);
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+}
+
+// Hashmin / SSSP with the superstep loop on the device (no per-superstep timing
+// and no per-instance counts): a few host synchronisations per run.
+ipg_status push_run_loop(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_stats* stats, cudaStream_t st,
+                         const char* name) {
+    const uint32_t n = g->n;
+    const bool recv = stats && (stats->flags & IPG_STAT_RECEIVERS);
+    const long long div = pull_divisor_for(g, kind == kSssp);
+    const bool pull = div > 0;
+    IPG_TRY(ensure_push_workspace(g, recv));
+    IPG_TRY(ensure_loop_workspace(g));
+    if (pull) {
+        IPG_TRY(ensure_csc(g, st));
+        IPG_TRY(pull_min_prepare(g, st));
+    }
+    cudaGraphExec_t& exec = g->push_exec[loop_slot(kind, recv, pull)];
+    if (!exec) IPG_TRY(push_loop_graph(g, kind, recv, pull, &exec));
+    IPG_CUDA(cudaMemsetAsync(g->stamp, 0, sizeof(uint32_t) * n, st));
+    if (recv) IPG_CUDA(cudaMemsetAsync(g->rstamp, 0, sizeof(uint32_t) * n, st));
+    IPG_CUDA(cudaMemsetAsync(&g->counters->status, 0, sizeof(unsigned), st));
+    uint32_t f;
+    if (kind == kHashmin) {
+        hashmin_init_kernel<<<grid_cap(n), 256, 0, st>>>(g->val, g->frontier[0], g->perm, n);
+        f = n;
+    } else {
+        sssp_init_kernel<<<grid_cap(n), 256, 0, st>>>(g->val, g->frontier[0], n, g->inv, source);
+        f = 1;
+    }
+    loop_init_kernel<<<1, 1, 0, st>>>(g->loop, f, (unsigned long long)(div > 0 ? div : 0));
+    IPG_CUDA(cudaGetLastError());
+    // each launch runs up to kLoopCap supersteps; a run has at most n + 1
+    const uint64_t max_launches = (uint64_t)n / kLoopCap + 3;
+    g->h_loop->done = 0;
+    for (uint64_t launches = 0; !g->h_loop->done; ++launches) {
+        if (launches > max_launches) return set_error(IPG_EDEVICE, "%s: the superstep loop did not end", name);
+        IPG_CUDA(cudaGraphLaunch(exec, st));
+        IPG_CUDA(cudaMemcpyAsync(g->h_loop, g->loop, sizeof(PushLoop), cudaMemcpyDeviceToHost, st));
+        IPG_CUDA(cudaStreamSynchronize(st));
+    }
+    const PushLoop h = *g->h_loop;
+    if (h.status & kStatusOverflow) return set_error(IPG_EOVERFLOW, "%s: a path length reached UINT32_MAX", name);
+    if (h.status) return set_error(IPG_EDEVICE, "%s: frontier overflow", name);
+    if (stats) {
+        const uint32_t keep = std::min(std::min(h.nrec, kLoopRecords), stats->cap);
+        if (keep && stats->buf)
+            IPG_CUDA(cudaMemcpyAsync(stats->buf, g->loop_rec, sizeof(ipg_superstep_stats) * keep,
+                                     cudaMemcpyDeviceToHost, st));
+        stats->count = h.count;
+    }
+    unpermute_u32_kernel<<<grid_cap(n), 256, 0, st>>>(g->val, g->inv, n, out);
+    IPG_CUDA(cudaGetLastError());
+    IPG_CUDA(cudaStreamSynchronize(st));
     return IPG_OK;
 }
 
@@ -451,6 +679,9 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
         }
         return IPG_OK;
     }
+    if (!timing && !(inst_supersteps && g->instances) && (!stats || stats->cap <= kLoopRecords) &&
+        tuning().push_loop != 0)
+        return push_run_loop(g, kind, source, out, stats, st, name);
     IPG_TRY(ensure_push_workspace(g, recv));
     uint32_t* val = g->val;
     cudaEvent_t* ev = nullptr;
@@ -510,7 +741,8 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
         } else {
             IPG_TRY(frontier_partition(g, f, st));
             if (timing) IPG_CUDA(cudaEventRecord(ev[1], st));
-            relax_dispatch(kind, recv, relax_grid, st, g, val, g->frontier[cur ^ 1], f, s + 1);
+            relax_dispatch(kind, recv, relax_grid, st, g, val, g->frontier[cur ^ 1], g->frontier[cur ^ 1], nullptr, f,
+                           s + 1);
             IPG_CUDA(cudaGetLastError());
         }
         if (timing) IPG_CUDA(cudaEventRecord(ev[2], st));
@@ -568,16 +800,17 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
 
 ipg_status frontier_prepare(ipg_graph* g, const uint32_t* F, uint32_t f, const uint32_t* val, cudaStream_t st) {
     const uint32_t nb = (f + kFrBlock - 1) / kFrBlock;
-    fr_reduce_kernel<<<nb, kFrThreads, 0, st>>>(F, f, g->off, g->block_sums);
-    fr_scan_kernel<<<1, kScanThreads, 0, st>>>(g->block_sums, nb, f, g->fr_prefix, g->counters);
-    fr_write_kernel<<<nb, kFrThreads, 0, st>>>(F, f, g->off, val, g->block_sums, g->fr_prefix, g->fr_rowstart,
-                                               g->fr_val);
+    const unsigned grid = nb ? nb : 1;
+    fr_reduce_kernel<<<grid, kFrThreads, 0, st>>>(F, F, f, nullptr, g->off, g->block_sums);
+    fr_scan_kernel<<<1, kScanThreads, 0, st>>>(g->block_sums, nb, f, nullptr, g->m, g->fr_prefix, g->counters);
+    fr_write_kernel<<<grid, kFrThreads, 0, st>>>(F, F, f, nullptr, g->off, val, g->block_sums, g->fr_prefix,
+                                                 g->fr_rowstart, g->fr_val);
     IPG_CUDA(cudaGetLastError());
     return IPG_OK;
 }
 
 ipg_status frontier_partition(ipg_graph* g, uint32_t f, cudaStream_t st) {
-    push_partition_kernel<<<(unsigned)sm_count(g->device) * 2, 256, 0, st>>>(g->fr_prefix, f, g->counters,
+    push_partition_kernel<<<(unsigned)sm_count(g->device) * 2, 256, 0, st>>>(g->fr_prefix, f, nullptr, g->counters,
                                                                             g->push_tile_row);
     IPG_CUDA(cudaGetLastError());
     return IPG_OK;

@@ -34,12 +34,21 @@ ALWAYS_PULL = 1 << 40  # any superstep with a message runs in pull form
 
 
 @pytest.fixture(params=["auto", "push", "pull"])
-def direction(request, ipg):
+def direction(request, ipg, driver):
     """Runs a Hashmin/SSSP test with the automatic push/pull switch, always push, or always pull."""
     old = ipg.ipg_get_tuning("pull_divisor")
     ipg.ipg_set_tuning("pull_divisor", {"auto": old, "push": 0, "pull": ALWAYS_PULL}[request.param])
     yield request.param
     ipg.ipg_set_tuning("pull_divisor", old)
+
+
+@pytest.fixture(params=["graph-loop", "host-loop"])
+def driver(request, ipg):
+    """... and with the superstep loop in a CUDA graph on the device, or driven from the host."""
+    old = ipg.ipg_get_tuning("push_loop")
+    ipg.ipg_set_tuning("push_loop", 1 if request.param == "graph-loop" else 0)
+    yield request.param
+    ipg.ipg_set_tuning("push_loop", old)
 
 
 def _create(ipg, g, directed=None):

@@ -21,6 +21,7 @@ KNOBS = {
     "pr_threads": ([256, 512], [128, 1024, 0]),
     "pr_carveout": ([-1, 0, 50, 100], [-2, 101]),
     "batch_divisor": ([0, 1, 6, 1 << 40], [-1]),
+    "push_loop": ([0, 1], [2, -1]),
 }
 
 
