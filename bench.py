@@ -319,8 +319,12 @@ def run_ours(a):
     sssp_kernel_ms = [sum(s.kernel_ms for s in sst) for _, sst in all_stats]
     sssp_ms = [sum(s.superstep_ms for s in sst) for _, sst in all_stats]
     sssp_supersteps = [len(sst) for _, sst in all_stats]
-    launches_per_step = (1 + 2 * PR_UPDATES) + statistics.mean(
-        1 + 5 * sum(1 for s in sst if s.senders > 0) for _, sst in all_stats)
+    # kernels of one step: PageRank init, (pull, fix-up) per superstep, unpermute; SSSP init,
+    # per superstep 3 frontier passes + (partition, relax) in push form or (scatter, pull,
+    # fix-up) in pull form, unpermute
+    launches_per_step = (2 + 2 * PR_UPDATES) + statistics.mean(
+        2 + sum(3 + (3 if s.flags & ipg.IPG_STAT_PULL else 2) for s in sst if s.senders > 0)
+        for _, sst in all_stats)
 
     # roofline for the kernel that dominates the step (by CUDA-event time in the timed region)
     peak, peak_kind = peak_hbm()
