@@ -92,7 +92,9 @@ struct PmEmit {
     uint32_t* q;          // shared-memory queue of this tile's new frontier vertices
     unsigned int* qn;     // shared-memory queue length
     unsigned int* nrecv;  // shared-memory receiver count
-    uint32_t* __restrict__ next;
+    uint32_t* next0;      // the next frontier: picked at each use, see loop_next
+    uint32_t* next1;
+    const PushLoop* loop;
     PushCounters* ctr;
     __device__ __forceinline__ void operator()(uint32_t row, uint32_t m) const {
         if (kRecv && m != kInf) atomicAdd(nrecv, 1u);
@@ -102,7 +104,7 @@ struct PmEmit {
             if (slot < kPmQueue)
                 q[slot] = row;
             else
-                next[atomicAdd(&ctr->next_size, 1u)] = row;
+                loop_next(next0, next1, loop)[atomicAdd(&ctr->next_size, 1u)] = row;
         }
     }
 };
@@ -115,7 +117,6 @@ __global__ void __launch_bounds__(kPmThreads) pull_min_kernel(
     uint64_t tiles, uint32_t n, uint64_t m, uint32_t* next0, uint32_t* next1, const PushLoop* __restrict__ loop,
     PushCounters* __restrict__ ctr) {
     if (pull_skip(loop)) return;
-    uint32_t* __restrict__ next = loop_next(next0, next1, loop);
     __shared__ MpShared<kPmThreads, kPmItems, uint32_t> sh;
     __shared__ uint32_t s_q[kPmQueue];
     __shared__ unsigned int s_qn, s_recv, s_base;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kPmThreads) pull_min_kernel(
         s_recv = 0;
     }
     PmGather<kAddWeight, kWeightKind> gather{csc_src, csc_w8, csc_w32, sval, &ctr->status};
-    PmEmit<kRecv> emit{val, s_q, &s_qn, &s_recv, next, ctr};
+    PmEmit<kRecv> emit{val, s_q, &s_qn, &s_recv, next0, next1, loop, ctr};
     for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         mp_tile<kPmThreads, kPmItems, MinU32>(sh, csc_off, n, m, tile_row, tile, tile_head, tile_tail, gather, emit);
         __syncthreads();
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(kPmThreads) pull_min_kernel(
             if (threadIdx.x == 0) s_base = atomicAdd(&ctr->next_size, qn);
             __syncthreads();
             const unsigned base = s_base;
+            uint32_t* __restrict__ next = loop_next(next0, next1, loop);  // picked here: no register for the tile walk
             for (unsigned k = threadIdx.x; k < qn; k += kPmThreads) next[base + k] = s_q[k];
             __syncthreads();
             if (threadIdx.x == 0) s_qn = 0;
