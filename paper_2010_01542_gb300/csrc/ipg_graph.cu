@@ -619,6 +619,7 @@ static void free_graph(ipg_graph* g) {
     f(g->counters);
     f(g->inst_base);
     f(g->inst_msgs);
+    f(g->inst_steps);
     delete[] g->inst_base_host;
     if (g->pr_exec) cudaGraphExecDestroy(g->pr_exec);
     for (auto& x : g->push_exec)

@@ -168,7 +168,7 @@ struct ipg_graph {
     ipg::PushLoop* loop = nullptr;            // device loop state (graph-driven runs)
     ipg_superstep_stats* loop_rec = nullptr;  // device stats records of a graph-driven run
     ipg::PushLoop* h_loop = nullptr;          // pinned mirror
-    cudaGraphExec_t push_exec[8] = {};        // loop graphs: kind x receivers x weight kind (ipg_push.cu)
+    cudaGraphExec_t push_exec[16] = {};       // loop graphs: program x receivers x pull x instances (ipg_push.cu)
 
     void* batch = nullptr;          // batched-SSSP workspace (ipg_batch.cu)
     void* generic = nullptr;        // general-combiner workspace (ipg_generic.cu)
@@ -179,6 +179,7 @@ struct ipg_graph {
     uint32_t* inst_base_host = nullptr;  // instances + 1
     uint32_t* inst_base = nullptr;       // device copy
     unsigned long long* inst_msgs = nullptr;  // device, per instance
+    uint32_t* inst_steps = nullptr;           // device, per instance: supersteps of a loop-driven run
 
     cudaStream_t stream = nullptr;  // used by the host-buffer entry points
     ipg::StepTimer timer;

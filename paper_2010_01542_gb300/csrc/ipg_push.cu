@@ -375,10 +375,13 @@ __device__ __forceinline__ uint32_t instance_of(const uint32_t* __restrict__ bas
 }
 
 // per-instance messages of this superstep: sum of the senders' out-degrees, by instance
-__global__ void instance_msgs_kernel(const uint32_t* __restrict__ F, uint32_t f, const uint64_t* __restrict__ off,
+__global__ void instance_msgs_kernel(const uint32_t* F0, const uint32_t* F1, uint32_t f,
+                                     const PushLoop* __restrict__ loop, const uint64_t* __restrict__ off,
                                      const uint32_t* __restrict__ perm, const uint32_t* __restrict__ bases,
                                      uint32_t count, unsigned long long* __restrict__ inst_msgs) {
     extern __shared__ unsigned long long s_acc[];
+    const uint32_t* __restrict__ F = loop_frontier(F0, F1, loop);
+    f = loop_f(f, loop);
     const bool local = count <= 2048;
     if (local)
         for (uint32_t k = threadIdx.x; k < count; k += blockDim.x) s_acc[k] = 0;
@@ -398,6 +401,22 @@ __global__ void instance_msgs_kernel(const uint32_t* __restrict__ F, uint32_t f,
     if (local)
         for (uint32_t k = threadIdx.x; k < count; k += blockDim.x)
             if (s_acc[k]) atomicAdd(&inst_msgs[k], s_acc[k]);
+}
+
+// loop-driven runs of a batch graph: one more superstep for every instance whose
+// vertices sent messages in this one; the per-instance sums restart at zero
+__global__ void instance_step_kernel(unsigned long long* __restrict__ inst_msgs, uint32_t count,
+                                     uint32_t* __restrict__ inst_steps) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        if (inst_msgs[i]) ++inst_steps[i];
+        inst_msgs[i] = 0;
+    }
+}
+
+__global__ void fill_u32_kernel(uint32_t* __restrict__ a, uint32_t count, uint32_t value) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) a[i] = value;
 }
 
 // labels in caller ids of the union -> instance-local ids
@@ -543,8 +562,10 @@ ipg_status ensure_events_push(size_t count, cudaEvent_t** evs) {
     return IPG_OK;
 }
 
-// loop-graph slot: program x receivers counting x pull form allowed
-int loop_slot(int kind, bool recv, bool pull) { return (kind == kSssp ? 4 : 0) + (recv ? 2 : 0) + (pull ? 1 : 0); }
+// loop-graph slot: program x receivers counting x pull form allowed x per-instance counts
+int loop_slot(int kind, bool recv, bool pull, bool inst) {
+    return (inst ? 8 : 0) + (kind == kSssp ? 4 : 0) + (recv ? 2 : 0) + (pull ? 1 : 0);
+}
 
 ipg_status ensure_loop_workspace(ipg_graph* g) {
     if (g->loop) return IPG_OK;
@@ -556,7 +577,7 @@ ipg_status ensure_loop_workspace(ipg_graph* g) {
 
 // Builds [WHILE (cond) { superstep }] for one slot.  The body enqueues both forms
 // of the superstep; each returns at once unless fr_scan_kernel picked it.
-ipg_status push_loop_graph(ipg_graph* g, int kind, bool recv, bool pull, cudaGraphExec_t* out) {
+ipg_status push_loop_graph(ipg_graph* g, int kind, bool recv, bool pull, bool inst, cudaGraphExec_t* out) {
     const int sms = sm_count(g->device);
     const unsigned fixed = (unsigned)sms * 8;
     cudaGraph_t graph = nullptr;
@@ -580,6 +601,13 @@ ipg_status push_loop_graph(ipg_graph* g, int kind, bool recv, bool pull, cudaGra
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "superstep loop graph", __FILE__, __LINE__);
             break;
+        }
+        if (inst) {  // per-instance messages of the senders, before the superstep changes anything
+            const size_t shm = g->instances <= 2048 ? sizeof(unsigned long long) * g->instances : 0;
+            instance_msgs_kernel<<<fixed, 256, shm, cap>>>(g->frontier[0], g->frontier[1], 0, g->loop, g->off,
+                                                           g->perm, g->inst_base, g->instances, g->inst_msgs);
+            instance_step_kernel<<<grid_cap(g->instances), 256, 0, cap>>>(g->inst_msgs, g->instances,
+                                                                         g->inst_steps);
         }
         fr_reduce_kernel<<<fixed, kFrThreads, 0, cap>>>(g->frontier[0], g->frontier[1], 0, g->loop, g->off,
                                                         g->block_sums);
@@ -605,19 +633,25 @@ ipg_status push_loop_graph(ipg_graph* g, int kind, bool recv, bool pull, cudaGra
 // Hashmin / SSSP with the superstep loop on the device (no per-superstep timing
 // and no per-instance counts): a few host synchronisations per run.
 ipg_status push_run_loop(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_stats* stats, cudaStream_t st,
-                         const char* name) {
+                         const char* name, uint32_t* inst_supersteps) {
     const uint32_t n = g->n;
     const bool recv = stats && (stats->flags & IPG_STAT_RECEIVERS);
     const long long div = pull_divisor_for(g, kind == kSssp);
     const bool pull = div > 0;
+    const bool inst = inst_supersteps && g->instances;
     IPG_TRY(ensure_push_workspace(g, recv));
     IPG_TRY(ensure_loop_workspace(g));
+    if (inst && !g->inst_steps) IPG_CUDA(cudaMalloc(&g->inst_steps, sizeof(uint32_t) * g->instances));
     if (pull) {
         IPG_TRY(ensure_csc(g, st));
         IPG_TRY(pull_min_prepare(g, st));
     }
-    cudaGraphExec_t& exec = g->push_exec[loop_slot(kind, recv, pull)];
-    if (!exec) IPG_TRY(push_loop_graph(g, kind, recv, pull, &exec));
+    cudaGraphExec_t& exec = g->push_exec[loop_slot(kind, recv, pull, inst)];
+    if (!exec) IPG_TRY(push_loop_graph(g, kind, recv, pull, inst, &exec));
+    if (inst) {  // every instance runs superstep 0
+        IPG_CUDA(cudaMemsetAsync(g->inst_msgs, 0, sizeof(unsigned long long) * g->instances, st));
+        fill_u32_kernel<<<grid_cap(g->instances), 256, 0, st>>>(g->inst_steps, g->instances, 1u);
+    }
     IPG_CUDA(cudaMemsetAsync(g->stamp, 0, sizeof(uint32_t) * n, st));
     if (recv) IPG_CUDA(cudaMemsetAsync(g->rstamp, 0, sizeof(uint32_t) * n, st));
     IPG_CUDA(cudaMemsetAsync(&g->counters->status, 0, sizeof(unsigned), st));
@@ -650,6 +684,9 @@ ipg_status push_run_loop(ipg_graph* g, int kind, uint32_t source, uint32_t* out,
                                      cudaMemcpyDeviceToHost, st));
         stats->count = h.count;
     }
+    if (inst)
+        IPG_CUDA(cudaMemcpyAsync(inst_supersteps, g->inst_steps, sizeof(uint32_t) * g->instances,
+                                 cudaMemcpyDeviceToHost, st));
     unpermute_u32_kernel<<<grid_cap(n), 256, 0, st>>>(g->val, g->inv, n, out);
     IPG_CUDA(cudaGetLastError());
     IPG_CUDA(cudaStreamSynchronize(st));
@@ -679,9 +716,8 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
         }
         return IPG_OK;
     }
-    if (!timing && !(inst_supersteps && g->instances) && (!stats || stats->cap <= kLoopRecords) &&
-        tuning().push_loop != 0)
-        return push_run_loop(g, kind, source, out, stats, st, name);
+    if (!timing && (!stats || stats->cap <= kLoopRecords) && tuning().push_loop != 0)
+        return push_run_loop(g, kind, source, out, stats, st, name, inst_supersteps);
     IPG_TRY(ensure_push_workspace(g, recv));
     uint32_t* val = g->val;
     cudaEvent_t* ev = nullptr;
@@ -717,8 +753,8 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
         if (per_inst) {
             IPG_CUDA(cudaMemsetAsync(g->inst_msgs, 0, sizeof(unsigned long long) * ninst, st));
             const size_t shm = ninst <= 2048 ? sizeof(unsigned long long) * ninst : 0;
-            instance_msgs_kernel<<<grid_cap(f), 256, shm, st>>>(g->frontier[cur], f, g->off, g->perm, g->inst_base,
-                                                                ninst, g->inst_msgs);
+            instance_msgs_kernel<<<grid_cap(f), 256, shm, st>>>(g->frontier[cur], g->frontier[cur], f, nullptr, g->off,
+                                                                g->perm, g->inst_base, ninst, g->inst_msgs);
             IPG_CUDA(cudaGetLastError());
             IPG_CUDA(cudaMemcpyAsync(h_inst.data(), g->inst_msgs, sizeof(unsigned long long) * ninst,
                                      cudaMemcpyDeviceToHost, st));

@@ -108,8 +108,18 @@ def test_batch_device_entry_and_errors(ipg):
 # many graphs in one object: Hashmin on every instance at once
 
 
+@pytest.fixture(params=["graph-loop", "host-loop"])
+def driver(request, ipg):
+    """The union's superstep loop (and its per-instance superstep counts) on the device in a
+    CUDA graph, or driven from the host."""
+    old = ipg.ipg_get_tuning("push_loop")
+    ipg.ipg_set_tuning("push_loop", 1 if request.param == "graph-loop" else 0)
+    yield request.param
+    ipg.ipg_set_tuning("push_loop", old)
+
+
 @pytest.fixture(params=["auto", "push", "pull"])
-def direction(request, ipg):
+def direction(request, ipg, driver):
     old = ipg.ipg_get_tuning("pull_divisor")
     ipg.ipg_set_tuning("pull_divisor", {"auto": old, "push": 0, "pull": 1 << 40}[request.param])
     yield request.param
