@@ -144,3 +144,19 @@ def test_pagerank_512_threads_within_tolerance(ipg):
         ipg.ipg_set_tuning("pr_threads", old)
         ipg.ipg_set_tuning("pr_engine", 0)
     h.destroy()
+
+
+def test_pagerank_captured_loop_matches_timed_loop(ipg):
+    """Without per-superstep timing PageRank replays a captured CUDA graph of its
+    supersteps; with timing it launches them one by one.  Both are the same kernels
+    in the same order: bit-identical ranks, including after the update count (and so
+    the captured graph) changes."""
+    g = gen.rmat(12, 16, seed=11)
+    h = ipg.ipg_graph_create(g.offsets, g.cols, None, g.n, g.m, True)
+    for updates in (10, 3, 10):
+        r_graph, c1, _ = ipg.ipg_pagerank(h, updates)
+        r_timed, c2, st = ipg.ipg_pagerank(h, updates, stats_flags=ipg.IPG_STAT_TIMING)
+        assert c1 == c2 == updates + 1
+        assert all(s.kernel_ms > 0 for s in st[:updates])
+        assert np.array_equal(r_graph.view(np.uint32), r_timed.view(np.uint32))
+    h.destroy()
