@@ -22,8 +22,9 @@
  *     memory on the device that was current when the graph was created.
  *   - A `stream` argument is a cudaStream_t passed as void* (NULL = the legacy
  *     default stream).  *_dev calls enqueue on that stream and return after
- *     the result is complete on it (the drivers read a few bytes back per
- *     superstep to decide termination).
+ *     the result is complete on it (the library reads a few bytes back to
+ *     decide termination: per superstep, or per 64 supersteps when the
+ *     superstep loop runs on the device).
  *   - Every call returns an ipg_status; on failure, ipg_last_error() gives a
  *     message for the calling thread, outputs are unspecified and the stats
  *     count is 0.
