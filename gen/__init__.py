@@ -243,12 +243,17 @@ class DeviceCSR:
     weights: "object" = None
     directed: bool = True
 
-    def to_host(self, pinned: bool = False) -> CSR:
+    def to_host(self, pinned: bool = False, alloc=None) -> CSR:
+        """Copy to host arrays: pageable, torch page-locked (``pinned``), or from ``alloc(shape, dtype)``."""
         import torch
 
         def cp(t, np_dtype):
             if t is None:
                 return None
+            if alloc is not None:
+                h = alloc(tuple(t.shape), np_dtype)
+                torch.from_numpy(h.view(np.dtype("i%d" % h.itemsize))).copy_(t)
+                return h
             h = torch.empty(t.shape, dtype=t.dtype, pin_memory=pinned)
             h.copy_(t)
             return h.numpy().view(np_dtype)

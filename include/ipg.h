@@ -18,7 +18,8 @@
  *     offsets[n] = m, offsets non-decreasing, every column < n.  Self-loops and
  *     parallel edges are allowed; each stored edge carries one message.
  *   - Plain pointers and sizes only.  "host" pointers are ordinary CPU memory
- *     (pinned memory makes copies faster); "dev" pointers are CUDA device
+ *     (page-locked memory, best from ipg_host_alloc, makes copies faster);
+ *     "dev" pointers are CUDA device
  *     memory on the device that was current when the graph was created.
  *   - A `stream` argument is a cudaStream_t passed as void* (NULL = the legacy
  *     default stream).  *_dev calls enqueue on that stream and return after
@@ -37,6 +38,7 @@
 #ifndef IPG_H
 #define IPG_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -130,6 +132,29 @@ void ipg_graph_destroy(ipg_graph* g);
 
 /* Sizes and kind of a graph (any output pointer may be NULL). */
 ipg_status ipg_graph_info(const ipg_graph* g, uint32_t* n, uint64_t* m, int* directed, int* weighted);
+
+/*
+ * ipg_host_alloc — page-locked host memory for the host-buffer calls.
+ *   bytes  size of the buffer; 0 sets *out = NULL and returns IPG_OK;
+ *   out    receives the buffer: zero-filled, aligned to the transparent huge
+ *          page size (2 MiB on most kernels) when bytes is at least that size,
+ *          else to the base page size.
+ * The memory is an anonymous mapping advised to use transparent huge pages
+ * and registered with the CUDA runtime (portable to every context).  Host <->
+ * device copies from it keep full speed in a long-lived process, where the
+ * runtime's own page-locked buffers can end up on scattered small pages and
+ * slow a large upload (ipg_graph_create of a 15 GB graph) to half speed.
+ * The caller owns the buffer and releases it with ipg_host_free.  Returns
+ * IPG_EINVAL for out = NULL, IPG_ENOMEM when the mapping or the page lock
+ * fails for lack of memory, IPG_ECUDA for any other CUDA runtime error
+ * (including no usable device).  Thread-safe.
+ */
+ipg_status ipg_host_alloc(size_t bytes, void** out);
+
+/* Release a buffer from ipg_host_alloc.  NULL is ignored; a pointer that
+ * ipg_host_alloc did not return (or one already freed) gives IPG_EINVAL and
+ * nothing is released.  Thread-safe. */
+ipg_status ipg_host_free(void* p);
 
 /*
  * ipg_pagerank — PageRank (Sec. VI-C), pull form over the in-edges ("single

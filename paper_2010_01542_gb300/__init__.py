@@ -667,3 +667,47 @@ class Server:
 
 
 __all__ += ["Server", "Completion", "IPG_Q_SSSP", "IPG_Q_HASHMIN", "IPG_Q_PAGERANK"]
+
+
+class HostBuffer:
+    """Page-locked host memory from ``ipg_host_alloc`` (huge-page backed where the kernel allows).
+
+    Freed with ``ipg_host_free`` when the object goes away; numpy arrays made by
+    ``host_empty`` keep it alive through their ``base``.
+    """
+
+    def __init__(self, nbytes: int):
+        fn = _fn("ipg_host_alloc", [ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)])
+        p = ctypes.c_void_p()
+        _check(fn(int(nbytes), ctypes.byref(p)))
+        self.ptr = p.value or 0
+        self.nbytes = int(nbytes)
+
+    @property
+    def __array_interface__(self):
+        return {"shape": (self.nbytes,), "typestr": "|u1", "data": (self.ptr, False), "version": 3}
+
+    def free(self):
+        if self.ptr:
+            _fn("ipg_host_free", [ctypes.c_void_p])(ctypes.c_void_p(self.ptr))
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def host_empty(shape, dtype) -> np.ndarray:
+    """A zero-filled numpy array in ``ipg_host_alloc`` memory, for fast host <-> device copies."""
+    dtype = np.dtype(dtype)
+    shape = (int(shape),) if np.isscalar(shape) else tuple(int(s) for s in shape)
+    count = int(np.prod(shape, dtype=np.int64))
+    if count == 0:
+        return np.zeros(shape, dtype=dtype)
+    raw = np.asarray(HostBuffer(count * dtype.itemsize))
+    return raw.view(dtype).reshape(shape)
+
+
+__all__ += ["HostBuffer", "host_empty"]

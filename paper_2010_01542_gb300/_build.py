@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libipg.so")
 SOURCES = ["ipg_graph.cu", "ipg_pagerank.cu", "ipg_push.cu", "ipg_pull_min.cu", "ipg_batch.cu", "ipg_server.cu",
-           "ipg_noalloc.cu", "ipg_generic.cu", "ipg_tune.cu"]
+           "ipg_noalloc.cu", "ipg_generic.cu", "ipg_tune.cu", "ipg_host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 

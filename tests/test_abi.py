@@ -67,3 +67,17 @@ def test_missing_library_fails_loudly(tmp_path):
 
     with pytest.raises(ipg.IpgLibraryMissing):
         ipg.load_library(str(tmp_path / "nope.so"))
+
+
+def test_host_alloc_argument_checks(lib):
+    """ipg_host_alloc / ipg_host_free reject bad arguments on the host, before any CUDA call."""
+    alloc, free = lib.ipg_host_alloc, lib.ipg_host_free
+    alloc.argtypes, alloc.restype = [ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int
+    free.argtypes, free.restype = [ctypes.c_void_p], ctypes.c_int
+    assert alloc(16, None) == 1
+    p = ctypes.c_void_p(1234)
+    assert alloc(0, ctypes.byref(p)) == 0 and p.value is None  # empty request: NULL, no mapping
+    assert free(None) == 0
+    junk = ctypes.create_string_buffer(64)
+    assert free(ctypes.addressof(junk)) == 1  # not from ipg_host_alloc: refused, nothing released
+    assert b"ipg_host_alloc" in lib.ipg_last_error()
