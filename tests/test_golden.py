@@ -1,7 +1,7 @@
 """Hand-worked examples under tests/golden/: small graphs whose results and per-superstep
 counters were derived by hand from the superstep model (Sec. I), the combining mailbox
-(Sec. III) and the three benchmarks (Sec. VI-C), each derivation written out in its
-fixture.  The paper prints no worked example, so these are the stored values that pin
+(Sec. III, also with wider messages: shortest-path tree, path counting) and the three
+benchmarks (Sec. VI-C), each derivation written out in its fixture.  The paper prints no worked example, so these are the stored values that pin
 the oracle (CPU tests) and the CUDA path (GPU tests) to something outside both."""
 import glob
 import json
@@ -38,7 +38,7 @@ def _cases():
 
 def test_every_program_has_a_fixture():
     programs = {json.load(open(p))["program"] for p in FIXTURES}
-    assert programs == {"pagerank", "hashmin", "sssp"}
+    assert programs == {"pagerank", "hashmin", "sssp", "sssp_tree", "bfs_paths"}
 
 
 @pytest.mark.parametrize("path", FIXTURES, ids=[os.path.basename(p)[:-5] for p in FIXTURES])
@@ -71,6 +71,10 @@ def _run_oracle(fx, offsets, cols, weights, case):
         return oracle.pagerank(n, offsets, cols, case["updates"])
     if fx["program"] == "hashmin":
         return oracle.hashmin(n, offsets, cols)
+    if fx["program"] == "sssp_tree":
+        return oracle.sssp_tree(n, offsets, cols, weights, case["source"])
+    if fx["program"] == "bfs_paths":
+        return oracle.bfs_paths(n, offsets, cols, case["source"])
     return oracle.sssp(n, offsets, cols, weights if case["weighted"] else None, case["source"])
 
 
@@ -84,6 +88,12 @@ def test_oracle_reproduces_hand_worked_example(path, i):
     if fx["program"] == "pagerank":
         want = np.array([float(Fraction(x)) for x in case["ranks"]])
         np.testing.assert_allclose(r.values, want, rtol=1e-14, atol=0)
+    elif fx["program"] == "sssp_tree":
+        np.testing.assert_array_equal(r.dist, np.asarray(case["dist"], dtype=np.uint32))
+        np.testing.assert_array_equal(r.parent, np.asarray(case["parent"], dtype=np.uint32))
+    elif fx["program"] == "bfs_paths":
+        np.testing.assert_array_equal(r.level, np.asarray(case["level"], dtype=np.uint32))
+        np.testing.assert_array_equal(r.paths, np.asarray(case["paths"], dtype=np.uint64))
     else:
         want = case["labels"] if fx["program"] == "hashmin" else case["dist"]
         np.testing.assert_array_equal(r.values, np.asarray(want, dtype=np.uint32))
@@ -120,6 +130,16 @@ def test_cuda_path_reproduces_hand_worked_example(ipg, path, i):
         h = ipg.ipg_graph_create(offsets, cols, None, n, m, False)
         vals, count, st = ipg.ipg_hashmin_cc(h, stats_flags=flags)
         np.testing.assert_array_equal(vals, np.asarray(case["labels"], dtype=np.uint32))
+    elif fx["program"] == "sssp_tree":
+        h = ipg.ipg_graph_create(offsets, cols, weights, n, m, True)
+        dist, parent, count, st = ipg.ipg_sssp_tree(h, case["source"], stats_flags=flags)
+        np.testing.assert_array_equal(dist, np.asarray(case["dist"], dtype=np.uint32))
+        np.testing.assert_array_equal(parent, np.asarray(case["parent"], dtype=np.uint32))
+    elif fx["program"] == "bfs_paths":
+        h = ipg.ipg_graph_create(offsets, cols, None, n, m, True)
+        level, paths, count, st = ipg.ipg_bfs_paths(h, case["source"], stats_flags=flags)
+        np.testing.assert_array_equal(level, np.asarray(case["level"], dtype=np.uint32))
+        np.testing.assert_array_equal(paths, np.asarray(case["paths"], dtype=np.uint64))
     else:
         h = ipg.ipg_graph_create(offsets, cols, weights if case["weighted"] else None, n, m, True)
         vals, count, st = ipg.ipg_sssp(h, case["source"], stats_flags=flags)
