@@ -69,8 +69,11 @@ def build(force: bool = False) -> str:
 def _lib():
     global _lib_handle
     if _lib_handle is None:
-        build()
-        lib = ctypes.CDLL(_SO)
+        path = os.environ.get("IPG_ORACLE_LIB")  # another build of the oracle (the mutation tests' mutants)
+        if not path:
+            build()
+            path = _SO
+        lib = ctypes.CDLL(path)
         vp, u32, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int
         lib.orc_hashmin.argtypes = [u32, vp, vp, vp, vp, u32, u32, ctypes.POINTER(u32)]
         lib.orc_hashmin.restype = i32
