@@ -96,7 +96,8 @@ typedef struct {
  *            paper's unweighted SSSP, Sec. VI-C);
  *   directed nonzero: arbitrary directed graph.  zero: undirected, stored with
  *            both directions of every edge (the paper's graphs, Sec. VI-B);
- *            the library does not check the symmetry.
+ *            creation does not check the symmetry (ipg_graph_check_symmetric
+ *            does, on request).
  * The CSR is validated on the device; a malformed one returns IPG_EINVAL.
  * The in-edge (CSC) copy needed by PageRank on a directed graph is built on
  * the first ipg_pagerank call and kept.
@@ -132,6 +133,24 @@ void ipg_graph_destroy(ipg_graph* g);
 
 /* Sizes and kind of a graph (any output pointer may be NULL). */
 ipg_status ipg_graph_info(const ipg_graph* g, uint32_t* n, uint64_t* m, int* directed, int* weighted);
+
+/*
+ * ipg_graph_check_symmetric — does the stored graph equal its reverse?
+ *   symmetric  out: 1 if the multiset of stored edges (u, v, w) equals the
+ *              multiset of their reverses (v, u, w) (w omitted for an
+ *              unweighted graph), else 0.  An undirected graph as the paper uses
+ *              them (Sec. VI-B: both directions of every edge stored, with the
+ *              same weight) gives 1; parallel edges count with multiplicity and
+ *              self-loops are their own reverse.
+ *   stream     cudaStream_t as void* (NULL = legacy default); the call returns
+ *              after the check is complete on it.
+ * ipg_graph_create does not run this check (it costs two sorts of the edges);
+ * call it once after creating a graph with directed = 0 to confirm the input.
+ * Works on directed and undirected graphs alike.  Temporary device memory: about
+ * 32 bytes per edge (unweighted) or 48 (weighted), freed before returning;
+ * IPG_ENOMEM if it cannot be had.  IPG_EINVAL for a NULL argument.
+ */
+ipg_status ipg_graph_check_symmetric(const ipg_graph* g, int* symmetric, void* stream);
 
 /*
  * ipg_host_alloc — page-locked host memory for the host-buffer calls.

@@ -210,6 +210,17 @@ def ipg_graph_info(g: Graph):
     return {"n": n.value, "m": m.value, "directed": bool(d.value), "weighted": bool(w.value)}
 
 
+def ipg_graph_check_symmetric(g: Graph, stream=None) -> bool:
+    """True if the stored edges (with weights) equal their reverses: an undirected graph's check."""
+    fn = _fn("ipg_graph_check_symmetric", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p])
+    sym = ctypes.c_int(-1)
+    _check(fn(g.handle, ctypes.byref(sym), _stream_ptr(stream)))
+    return bool(sym.value)
+
+
+__all__ += ["ipg_graph_check_symmetric"]
+
+
 class _Stats:
     def __init__(self, flags: int, cap: int):
         self.arr = (_CStats * max(cap, 1))()

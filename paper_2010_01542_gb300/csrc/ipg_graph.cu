@@ -715,6 +715,141 @@ ipg_status create_graph(const uint64_t* offsets, const uint32_t* columns, const 
     return create_impl(offsets, columns, weights, n, m, directed, user_stream, from_device, out);
 }
 
+// ---------------------------------------------------------------------------
+// Symmetry check: does the stored edge multiset, weights included, equal its
+// reverse?  Both lists are sorted into (key, weight) order and compared entry by
+// entry.  Keys are (u << 32 | v) for the forward list and (v << 32 | u) for the
+// reverse one, built from the internal (renumbered) CSR: renumbering maps both
+// endpoints through one bijection, so it changes no answer.
+
+__global__ void sym_keys_kernel(const uint64_t* __restrict__ off, const uint32_t* __restrict__ col, uint32_t n,
+                                unsigned long long* __restrict__ fwd, unsigned long long* __restrict__ rev) {
+    // one warp per row
+    uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t lane = threadIdx.x & 31;
+    uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t u = warp; u < n; u += nwarps) {
+        uint64_t b = off[u], e = off[u + 1];
+        for (uint64_t p = b + lane; p < e; p += 32) {
+            const unsigned long long v = col[p];
+            fwd[p] = ((unsigned long long)u << 32) | v;
+            rev[p] = (v << 32) | u;
+        }
+    }
+}
+
+__global__ void sym_widen_kernel(const uint8_t* __restrict__ w8, uint64_t m, uint32_t* __restrict__ w) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) w[i] = w8[i];
+}
+
+__global__ void sym_compare_kernel(const unsigned long long* __restrict__ a, const unsigned long long* __restrict__ b,
+                                   const uint32_t* __restrict__ wa, const uint32_t* __restrict__ wb, uint64_t m,
+                                   unsigned int* __restrict__ differ) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+        bad |= a[i] != b[i] || (wa && wa[i] != wb[i]);
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(differ, 1u);
+}
+
+ipg_status check_symmetric(const ipg_graph* g, int* symmetric, cudaStream_t st) {
+    using ull = unsigned long long;
+    const uint64_t m = g->m;
+    const uint32_t n = g->n;
+    *symmetric = 1;
+    if (m == 0) return IPG_OK;
+    const bool weighted = g->w8 || g->w;
+    const int sms = device_sms(g->device);
+    int bits = 1;
+    while (bits < 32 && (1ull << bits) < (uint64_t)n) ++bits;
+    const int key_bits = 32 + bits;       // keys are (hi << 32 | lo) with hi, lo < 2^bits
+    const int w_bits = g->w8 ? 8 : 32;
+    const unsigned grid = grid_for(m, sms, 16);
+    ull *fwd = nullptr, *rev = nullptr, *tmp = nullptr;
+    uint32_t *w = nullptr, *w2 = nullptr, *wf = nullptr;
+    unsigned int* differ = nullptr;
+    unsigned int h_differ = 0;
+    void* temp = nullptr;
+    size_t temp_bytes = 0, tb = 0;
+    ipg_status rc = IPG_OK;
+    cudaError_t e = cudaSuccess;
+#define SYM_CUDA(call)                                             \
+    do {                                                           \
+        e = (call);                                                \
+        if (e != cudaSuccess) {                                    \
+            rc = cuda_fail(e, #call, __FILE__, __LINE__);          \
+            goto done;                                             \
+        }                                                          \
+    } while (0)
+    {
+        SYM_CUDA(cudaMalloc(&fwd, sizeof(ull) * m));
+        SYM_CUDA(cudaMalloc(&rev, sizeof(ull) * m));
+        SYM_CUDA(cudaMalloc(&tmp, sizeof(ull) * m));
+        SYM_CUDA(cudaMalloc(&differ, sizeof(unsigned int)));
+        SYM_CUDA(cudaMemsetAsync(differ, 0, sizeof(unsigned int), st));
+        sym_keys_kernel<<<grid_for((uint64_t)n * 32, sms, 16), 256, 0, st>>>(g->off, g->col, n, fwd, rev);
+        SYM_CUDA(cudaGetLastError());
+        if (!weighted) {
+            SYM_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, temp_bytes, (const ull*)nullptr, (ull*)nullptr,
+                                                    (long long)m, 0, key_bits, st));
+            SYM_CUDA(cudaMalloc(&temp, temp_bytes ? temp_bytes : 16));
+            SYM_CUDA(cub::DeviceRadixSort::SortKeys(temp, temp_bytes, (const ull*)fwd, tmp, (long long)m, 0, key_bits,
+                                                    st));  // tmp: forward, sorted
+            SYM_CUDA(cub::DeviceRadixSort::SortKeys(temp, temp_bytes, (const ull*)rev, fwd, (long long)m, 0, key_bits,
+                                                    st));  // fwd: reverse, sorted
+            sym_compare_kernel<<<grid, 256, 0, st>>>(tmp, fwd, nullptr, nullptr, m, differ);
+            SYM_CUDA(cudaGetLastError());
+        } else {
+            SYM_CUDA(cudaMalloc(&w, sizeof(uint32_t) * m));
+            SYM_CUDA(cudaMalloc(&w2, sizeof(uint32_t) * m));
+            SYM_CUDA(cudaMalloc(&wf, sizeof(uint32_t) * m));
+            if (g->w8) {
+                sym_widen_kernel<<<grid, 256, 0, st>>>(g->w8, m, w);
+                SYM_CUDA(cudaGetLastError());
+            } else {
+                SYM_CUDA(cudaMemcpyAsync(w, g->w, sizeof(uint32_t) * m, cudaMemcpyDeviceToDevice, st));
+            }
+            SYM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, (const uint32_t*)nullptr, (uint32_t*)nullptr,
+                                                     (const ull*)nullptr, (ull*)nullptr, (long long)m, 0, w_bits, st));
+            temp_bytes = tb;
+            SYM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, (const ull*)nullptr, (ull*)nullptr,
+                                                     (const uint32_t*)nullptr, (uint32_t*)nullptr, (long long)m, 0,
+                                                     key_bits, st));
+            if (tb > temp_bytes) temp_bytes = tb;
+            SYM_CUDA(cudaMalloc(&temp, temp_bytes ? temp_bytes : 16));
+            // each list: by weight, then stably by key, which leaves it in (key, weight) order
+            SYM_CUDA(cub::DeviceRadixSort::SortPairs(temp, temp_bytes, (const uint32_t*)w, w2, (const ull*)fwd, tmp,
+                                                     (long long)m, 0, w_bits, st));
+            SYM_CUDA(cub::DeviceRadixSort::SortPairs(temp, temp_bytes, (const ull*)tmp, fwd, (const uint32_t*)w2, wf,
+                                                     (long long)m, 0, key_bits, st));  // (fwd, wf): forward
+            SYM_CUDA(cub::DeviceRadixSort::SortPairs(temp, temp_bytes, (const uint32_t*)w, w2, (const ull*)rev, tmp,
+                                                     (long long)m, 0, w_bits, st));
+            SYM_CUDA(cub::DeviceRadixSort::SortPairs(temp, temp_bytes, (const ull*)tmp, rev, (const uint32_t*)w2, w,
+                                                     (long long)m, 0, key_bits, st));  // (rev, w): reverse
+            sym_compare_kernel<<<grid, 256, 0, st>>>(fwd, rev, wf, w, m, differ);
+            SYM_CUDA(cudaGetLastError());
+        }
+        SYM_CUDA(cudaMemcpyAsync(&h_differ, differ, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
+        SYM_CUDA(cudaStreamSynchronize(st));
+        *symmetric = h_differ ? 0 : 1;
+    }
+done:
+#undef SYM_CUDA
+    if (fwd) cudaFree(fwd);
+    if (rev) cudaFree(rev);
+    if (tmp) cudaFree(tmp);
+    if (w) cudaFree(w);
+    if (w2) cudaFree(w2);
+    if (wf) cudaFree(wf);
+    if (differ) cudaFree(differ);
+    if (temp) cudaFree(temp);
+    if (rc != IPG_OK && e == cudaErrorMemoryAllocation)
+        return set_error(IPG_ENOMEM, "ipg_graph_check_symmetric: temporary device memory (about %d bytes per edge) "
+                                     "could not be allocated", weighted ? 48 : 32);
+    return rc;
+}
+
 }  // namespace ipg
 
 using namespace ipg;
@@ -833,6 +968,14 @@ ipg_status ipg_graph_info(const ipg_graph* g, uint32_t* n, uint64_t* m, int* dir
     if (directed) *directed = g->directed;
     if (weighted) *weighted = g->weighted;
     return IPG_OK;
+}
+
+ipg_status ipg_graph_check_symmetric(const ipg_graph* g, int* symmetric, void* stream) {
+    if (!g) return set_error(IPG_EINVAL, "ipg_graph_check_symmetric: graph is NULL");
+    if (!symmetric) return set_error(IPG_EINVAL, "ipg_graph_check_symmetric: symmetric is NULL");
+    DeviceGuard guard(g->device);
+    if (!guard.ok) return set_error(IPG_ECUDA, "ipg_graph_check_symmetric: cannot select the graph's device");
+    return check_symmetric(g, symmetric, static_cast<cudaStream_t>(stream));
 }
 
 const char* ipg_last_error(void) { return g_err; }
