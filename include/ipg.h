@@ -53,7 +53,8 @@ typedef enum {
     IPG_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
     IPG_EDEVICE = 5,   /* a kernel reported an internal inconsistency */
     IPG_ENOTSUP = 6,   /* operation not supported for this graph */
-    IPG_EOVERFLOW = 7  /* an SSSP distance would reach UINT32_MAX */
+    IPG_EOVERFLOW = 7, /* an SSSP distance would reach UINT32_MAX */
+    IPG_ECANCELED = 8  /* a served query was cancelled before it was dispatched */
 } ipg_status;
 
 typedef struct ipg_graph ipg_graph; /* opaque; owns its device copy */
@@ -411,6 +412,14 @@ ipg_status ipg_server_submit(ipg_server* s, const ipg_query* q);
 /* Up to cap completed queries into out; waits up to wait_ms for the first one
  * (0: no wait, < 0: until one completes or nothing is in flight). */
 uint32_t ipg_server_poll(ipg_server* s, ipg_completion* out, uint32_t cap, int wait_ms);
+/* Cancel every queued query whose user tag equals `user` and that no worker has
+ * dispatched yet.  Each completes at once with status IPG_ECANCELED (supersteps
+ * 0, batch 0, t_start = t_done = the time of the cancel); its out buffer is not
+ * written and is the caller's again after that completion is polled.  A query
+ * already dispatched runs to completion: no running kernel is interrupted.
+ * *cancelled (may be NULL) receives the number cancelled.  IPG_EINVAL for a
+ * NULL server. */
+ipg_status ipg_server_cancel(ipg_server* s, uint64_t user, uint32_t* cancelled);
 /* Wait until every submitted query has completed (completions stay pollable). */
 ipg_status ipg_server_drain(ipg_server* s);
 /* Seconds since the server was created (the clock of the completion times). */

@@ -26,9 +26,9 @@ __all__ = [
     "IPG_STAT_RECEIVERS", "IPG_STAT_TIMING", "IPG_STAT_PULL", "INF", "load_library",
 ]
 
-IPG_OK, IPG_EINVAL, IPG_ENOMEM, IPG_ECUDA, IPG_ETIMEOUT, IPG_EDEVICE, IPG_ENOTSUP, IPG_EOVERFLOW = range(8)
+IPG_OK, IPG_EINVAL, IPG_ENOMEM, IPG_ECUDA, IPG_ETIMEOUT, IPG_EDEVICE, IPG_ENOTSUP, IPG_EOVERFLOW, IPG_ECANCELED = range(9)
 STATUS_NAMES = ["IPG_OK", "IPG_EINVAL", "IPG_ENOMEM", "IPG_ECUDA", "IPG_ETIMEOUT", "IPG_EDEVICE", "IPG_ENOTSUP",
-                "IPG_EOVERFLOW"]
+                "IPG_EOVERFLOW", "IPG_ECANCELED"]
 IPG_STAT_RECEIVERS = 1
 IPG_STAT_TIMING = 2
 IPG_STAT_PULL = 4
@@ -627,6 +627,8 @@ class Server:
         lib.ipg_server_submit.restype = ctypes.c_int
         lib.ipg_server_poll.argtypes = [ctypes.c_void_p, ctypes.POINTER(_CCompletion), ctypes.c_uint32, ctypes.c_int]
         lib.ipg_server_poll.restype = ctypes.c_uint32
+        lib.ipg_server_cancel.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32)]
+        lib.ipg_server_cancel.restype = ctypes.c_int
         lib.ipg_server_drain.argtypes = [ctypes.c_void_p]
         lib.ipg_server_drain.restype = ctypes.c_int
         lib.ipg_server_now.argtypes = [ctypes.c_void_p]
@@ -658,6 +660,13 @@ class Server:
             res.append(Completion(int(c.user), int(c.status), int(c.supersteps), int(c.batch), float(c.t_submit),
                                   float(c.t_start), float(c.t_done), self._outs.pop(int(c.user), None)))
         return res
+
+    def cancel(self, user: int) -> int:
+        """Cancel the queued, not yet dispatched queries tagged `user`; returns how many.
+        Each still produces a completion (status IPG_ECANCELED) for poll()."""
+        k = ctypes.c_uint32(0)
+        _check(self._lib.ipg_server_cancel(self._h, user, ctypes.byref(k)))
+        return int(k.value)
 
     def drain(self):
         _check(self._lib.ipg_server_drain(self._h))

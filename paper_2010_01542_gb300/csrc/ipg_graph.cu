@@ -990,6 +990,7 @@ const char* ipg_status_string(ipg_status s) {
         case IPG_EDEVICE: return "IPG_EDEVICE";
         case IPG_ENOTSUP: return "IPG_ENOTSUP";
         case IPG_EOVERFLOW: return "IPG_EOVERFLOW";
+        case IPG_ECANCELED: return "IPG_ECANCELED";
     }
     return "IPG_UNKNOWN";
 }

@@ -17,7 +17,8 @@
 // fits next to the others (free device memory minus a reserve, or a fixed
 // budget); if not, it releases the workspace of idle graphs, least recently
 // used first, and otherwise waits for running work to finish.  Results go to
-// the caller's host buffers; completions carry timestamps for latency.
+// the caller's host buffers; completions carry timestamps for latency.  A query
+// can be cancelled until a worker dispatches it.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -391,6 +392,38 @@ uint32_t ipg_server_poll(ipg_server* s, ipg_completion* out, uint32_t cap, int w
         s->done.pop_front();
     }
     return k;
+}
+
+ipg_status ipg_server_cancel(ipg_server* s, uint64_t user, uint32_t* cancelled) {
+    if (!s) return set_error(IPG_EINVAL, "ipg_server_cancel: server is NULL");
+    uint32_t k = 0;
+    {
+        // workers take queries off the queues under this lock, so each query is
+        // either still queued here (and cancelled) or already dispatched
+        std::lock_guard<std::mutex> lock(s->mu);
+        const double t = s->now();
+        for (auto& sl : s->slots) {
+            for (auto it = sl.pending.begin(); it != sl.pending.end();) {
+                if (it->q.user != user) {
+                    ++it;
+                    continue;
+                }
+                ipg_completion c{};
+                c.user = user;
+                c.status = IPG_ECANCELED;
+                c.t_submit = it->t_submit;
+                c.t_start = t;
+                c.t_done = t;
+                s->done.push_back(c);
+                it = sl.pending.erase(it);
+                ++k;
+            }
+        }
+        s->inflight -= k;
+    }
+    if (k) s->cv_done.notify_all();
+    if (cancelled) *cancelled = k;
+    return IPG_OK;
 }
 
 ipg_status ipg_server_drain(ipg_server* s) {

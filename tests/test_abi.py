@@ -49,6 +49,9 @@ def test_pure_host_calls(lib):
     assert ipg.ipg_version() >= 100
     assert lib.ipg_status_string(0) == b"IPG_OK"
     assert lib.ipg_status_string(7) == b"IPG_EOVERFLOW"
+    assert lib.ipg_status_string(8) == b"IPG_ECANCELED"
+    assert ipg.STATUS_NAMES[ipg.IPG_ECANCELED] == "IPG_ECANCELED"
+    assert lib.ipg_server_cancel(None, 0, None) == 1
     # a NULL graph is rejected on the host, before any CUDA call
     assert lib.ipg_graph_info(None, None, None, None, None) == 1
     assert b"NULL" in lib.ipg_last_error()

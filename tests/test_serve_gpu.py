@@ -108,3 +108,48 @@ def test_server_rejects_bad_queries(ipg):
     assert c.user == 5 and c.status == 0 and c.supersteps == cnt
     np.testing.assert_array_equal(c.out, ref)
     srv.close()
+
+
+def test_cancel_queued_queries(ipg):
+    """Queries cancelled while queued complete with IPG_ECANCELED and leave their output
+    untouched; the others still equal ipg_sssp alone.  One worker is kept busy on another
+    graph (a long PageRank) so that the SSSP queries queue up behind it."""
+    big = gen.rmat(16, 16, seed=7, undirected=True, weighted=True)
+    small = gen.rmat(10, 16, seed=8, undirected=True, weighted=True)
+    hb = ipg.ipg_graph_create(big.offsets, big.cols, big.weights, big.n, big.m, False)
+    hs = ipg.ipg_graph_create(small.offsets, small.cols, small.weights, small.n, small.m, False)
+    ref = {u: ipg.ipg_sssp(hs, u)[:2] for u in range(20)}
+    cancelled_total = 0
+    for _ in range(3):  # a cancel can lose the race with a free worker; retry the scenario
+        srv = ipg.Server([hb, hs], workers=1, min_sssp_batch=1000)  # SSSP one source at a time
+        srv.submit(0, ipg.IPG_Q_PAGERANK, np.empty(big.n, dtype=np.float32), updates=300, user=1000)
+        outs = {}
+        for u in range(20):
+            outs[u] = np.full(small.n, 0xA5A5A5A5, dtype=np.uint32)
+            srv.submit(1, ipg.IPG_Q_SSSP, outs[u], source=u, user=u)
+        k = sum(srv.cancel(u) for u in range(0, 20, 2))
+        assert srv.cancel(12345) == 0  # no such query
+        srv.drain()
+        done = srv.poll(0)
+        srv.close()
+        by_user = {c.user: c for c in done}
+        assert len(done) == 21 and len(by_user) == 21
+        assert by_user[1000].status == 0
+        n_cancel = 0
+        for u in range(20):
+            c = by_user[u]
+            if c.status == ipg.IPG_ECANCELED:
+                assert u % 2 == 0
+                assert c.supersteps == 0 and c.batch == 0 and c.t_start == c.t_done
+                assert np.all(outs[u] == 0xA5A5A5A5)  # never written
+                n_cancel += 1
+            else:
+                assert c.status == 0
+                vals, cnt = ref[u]
+                np.testing.assert_array_equal(c.out, vals)
+                assert c.supersteps == cnt
+        assert n_cancel == k
+        cancelled_total += k
+        if k:
+            break
+    assert cancelled_total > 0
