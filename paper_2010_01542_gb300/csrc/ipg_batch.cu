@@ -130,6 +130,13 @@ __device__ __forceinline__ void batch_flush(uint32_t v, uint32_t run, uint32_t l
     }
 }
 
+// end of a row relative to the start of a chunk, clamped to 32 bits: a chunk holds at
+// most kChunk edges, so every value from kChunk up means "ends after this chunk"
+__device__ __forceinline__ uint32_t chunk_rel_end(uint64_t row_end, uint64_t e_begin) {
+    const uint64_t r = row_end - e_begin;
+    return r < 0xFFFFFFFFull ? (uint32_t)r : 0xFFFFFFFFu;
+}
+
 template <int kWeightKind>
 __global__ void __launch_bounds__(256) batch_pull_kernel(
     const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ csc_src, const uint8_t* __restrict__ w8,
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
         const uint64_t e_begin = c * kChunk;
         const uint32_t len = (uint32_t)(e_begin + kChunk < m ? kChunk : m - e_begin);
         uint32_t row = chunk_row[c];
-        uint32_t bound = (uint32_t)(csc_off[row + 1] - e_begin);  // row end, relative to the chunk (may exceed len)
+        uint32_t bound = chunk_rel_end(csc_off[row + 1], e_begin);  // row end, relative to the chunk (may exceed len)
         uint32_t run = kInf;
         bool pending = false;  // some lane folded a message into run (warp-uniform)
         for (uint32_t j0 = 0; j0 < len; j0 += 32) {
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
                             pending = false;
                             do {
                                 ++row;
-                                bound = (uint32_t)(csc_off[row + 1] - e_begin);
+                                bound = chunk_rel_end(csc_off[row + 1], e_begin);
                             } while (e >= bound);
                         }
                         if (s[q] < lim[q]) {
