@@ -85,3 +85,36 @@ def test_host_alloc_argument_checks(lib):
     junk = ctypes.create_string_buffer(64)
     assert free(ctypes.addressof(junk)) == 1  # not from ipg_host_alloc: refused, nothing released
     assert b"ipg_host_alloc" in lib.ipg_last_error()
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path, lib):
+    """A C99 program built against include/ipg.h and linked with libipg.so calls the
+    host-side entry points (no GPU needed): version, status names, argument errors."""
+    from paper_2010_01542_gb300 import _build
+
+    libdir = os.path.dirname(_build.library_path())
+    src = tmp_path / "use_ipg.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "ipg.h"
+int main(void) {
+    if (ipg_version() < 100) return 1;
+    if (strcmp(ipg_status_string(IPG_EINVAL), "IPG_EINVAL") != 0) return 2;
+    if (ipg_graph_info(NULL, NULL, NULL, NULL, NULL) != IPG_EINVAL) return 3;
+    if (strlen(ipg_last_error()) == 0) return 4;
+    ipg_graph* g = NULL;
+    if (ipg_graph_create(NULL, NULL, NULL, 0, 0, 1, &g) != IPG_EINVAL || g != NULL) return 5;
+    void* p = (void*)1;
+    if (ipg_host_alloc(0, &p) != IPG_OK || p != NULL) return 6;
+    if (ipg_server_cancel(NULL, 0, NULL) != IPG_EINVAL) return 7;
+    ipg_graph_destroy(NULL);
+    puts("ok");
+    return 0;
+}
+''')
+    exe = tmp_path / "use_ipg"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-L", libdir, "-lipg", "-Wl,-rpath," + libdir, "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
