@@ -5,6 +5,7 @@ import glob
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -118,3 +119,44 @@ int main(void) {
                            "-L", libdir, "-lipg", "-Wl,-rpath," + libdir, "-o", str(exe)])
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
+
+
+_NULL_PROBE = r'''
+import ctypes, re, sys
+import paper_2010_01542_gb300 as ipg
+lib = ipg.load_library()
+text = re.sub(r"/\*.*?\*/", "", open(sys.argv[1]).read(), flags=re.S)
+bad = []
+seen = 0
+for m in re.finditer(r"^\s*(ipg_status|uint32_t|double|void)\s+(ipg_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.M):
+    ret, name, params = m.groups()
+    ps = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+    if not ps or not re.search(r"\b(ipg_graph|ipg_server)\s*\*", ps[0]):
+        continue
+    fn = getattr(lib, name)
+    fn.argtypes = None
+    fn.restype = {"ipg_status": ctypes.c_int, "uint32_t": ctypes.c_uint32, "double": ctypes.c_double}.get(ret)
+    args = [ctypes.c_void_p(None) if "*" in p else ctypes.c_double(0) if "double" in p
+            else ctypes.c_uint64(0) if "64" in p else ctypes.c_uint32(0) for p in ps]
+    r = fn(*args)
+    seen += 1
+    if ret == "ipg_status" and r != 1:
+        bad.append((name, r))
+    if ret in ("uint32_t", "double") and r != 0:
+        bad.append((name, r))
+print(seen, bad)
+'''
+
+
+def test_every_handle_entry_point_rejects_null(tmp_path, lib):
+    """Each entry point whose first argument is a graph or server handle, called with NULL
+    for every pointer and 0 for every number, returns IPG_EINVAL (or 0 / nothing) on the
+    host before any CUDA call, and nothing crashes.  Runs in a child process."""
+    script = tmp_path / "null_probe.py"
+    script.write_text(_NULL_PROBE)
+    env = dict(os.environ, PYTHONPATH=ROOT + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, str(script), os.path.join(ROOT, "include", "ipg.h")], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    seen, bad = r.stdout.strip().rsplit("\n", 1)[-1].split(" ", 1)
+    assert int(seen) >= 20 and bad == "[]", r.stdout
