@@ -11,7 +11,8 @@ e2e        the same metric through the host-buffer C ABI: ipg_graph_create from 
            CSR in page-locked ipg_host_alloc memory (upload + in-edge build),
            ipg_pagerank and ipg_sssp into host arrays, ipg_graph_destroy, every step.
 roofline   the dominant kernel's algorithmic bytes per launch / its mean CUDA-event
-           duration, against the measured HBM copy bandwidth.
+           duration, against the measured HBM copy bandwidth (frac) and the nominal
+           7.9 TB/s (frac_of_nominal).
 cpu_baseline  the CPU oracle (single thread) on a bounded sample of the same graph.
 
 Multi-GPU: the path does not shard here; with --gpus N every rank runs its own replica
@@ -249,6 +250,9 @@ def measured_traffic(kernel, workload):
     return d["dram_bytes_per_launch"]
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
 def peak_hbm():
     try:
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -359,6 +363,7 @@ def run_ours(a):
     share = kd["total_ms"] / sum(k["total_ms"] for k in kernels.values())
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kd["achieved_gbs"], "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": round(kd["achieved_gbs"] / peak, 4),
+                "frac_of_nominal": round(kd["achieved_gbs"] / NOMINAL_HBM_GBS, 4),
                 "traffic": None if kd["traffic_per_launch"] is None else int(kd["traffic_per_launch"]),
                 "algorithmic_bytes_per_launch": kd["algorithmic_bytes_per_launch"],
                 "share_of_kernel_time": round(share, 3)}
@@ -643,6 +648,7 @@ def run_small_config(a, kind):
                            "l2": "graph L2-resident: latency- and launch-bound at this size"},
                 "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                              "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                             "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                              "traffic": None, "algorithmic_bytes_per_launch": int(bpl), "bytes_rule": rule},
                 "cpu_baseline": cpu, "autotune": tune, "clocks": clocks,
                 "gpu_launches": ((1 + 2 * PR_UPDATES + 1) if pr else
