@@ -54,3 +54,17 @@ def test_our_arm_fails_loudly_without_a_gpu():
                 "--no-cpu-baseline"])
     assert r.returncode != 0
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_cpu_parallel_baseline_entry():
+    """The bench's OpenMP baseline entry on a small graph: a positive rate, the threads used,
+    and a description of the sample; errors would come back as an `unavailable` entry."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import gen
+
+    g = gen.rmat(12, 8, seed=3, weighted=True)
+    d = bench.cpu_parallel_baseline(g, int(gen.max_out_degree_vertex(g)), 0.2)
+    assert "unavailable" not in d, d
+    assert d["value"] > 0 and d["cores"] >= 1 and d["unit"] == "GTEPS" and "OpenMP" in d["kind"]
+    assert "source rows" in d["sample"]
