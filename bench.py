@@ -252,6 +252,21 @@ def cpu_parallel_baseline(g, src, seconds):
         return {"unavailable": f"{type(e).__name__}: {e}"[:300]}
 
 
+def cpu_parallel_whole(g, pagerank: bool):
+    """The OpenMP baseline on the whole graph: PageRank (10 updates) or Hashmin to quiescence."""
+    try:
+        import cpu_baseline as omp_baseline
+
+        r = (omp_baseline.pagerank(g.n, g.offsets, g.cols, PR_UPDATES) if pagerank
+             else omp_baseline.hashmin(g.n, g.offsets, g.cols))
+        return {"value": round(r.messages / r.seconds / 1e9, 4), "unit": UNIT, "cores": omp_baseline.threads(),
+                "kind": "paper design: OpenMP, pull " + ("PageRank" if pagerank else "Hashmin") + ", dynamic 256",
+                "sample": f"the whole graph: {r.messages} messages in {r.seconds:.3f} s of supersteps, "
+                          f"{r.supersteps} supersteps"}
+    except Exception as e:  # noqa: BLE001 - a baseline must not take the bench down
+        return {"unavailable": f"{type(e).__name__}: {e}"[:300]}
+
+
 # ---------------------------------------------------------------------------------------
 # roofline helpers
 
@@ -656,8 +671,9 @@ def run_small_config(a, kind):
     dom = max(kern, key=lambda k: kern[k][1])
     nl, kms, bpl = kern[dom]
     achieved = bpl * nl / (kms / 1e3) / 1e9
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and not a.no_cpu_baseline:
+        cpu_par = cpu_parallel_whole(g, pr)
         t0 = time.perf_counter()
         ref = oracle.pagerank(g.n, g.offsets, g.cols, PR_UPDATES) if pr else oracle.hashmin(g.n, g.offsets, g.cols)
         t = time.perf_counter() - t0
@@ -684,7 +700,7 @@ def run_small_config(a, kind):
                              "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                              "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                              "traffic": None, "algorithmic_bytes_per_launch": int(bpl), "bytes_rule": rule},
-                "cpu_baseline": cpu, "autotune": tune, "clocks": clocks,
+                "cpu_baseline": cpu, "cpu_parallel": cpu_par, "autotune": tune, "clocks": clocks,
                 "gpu_launches": ((1 + 2 * PR_UPDATES + 1) if pr else
                                  (1 + 5 * sum(1 for s in st if s.senders) + 1)) * a.steps,
                 "messages_per_superstep": [s.messages_sent for s in st]}

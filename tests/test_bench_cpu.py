@@ -68,3 +68,15 @@ def test_cpu_parallel_baseline_entry():
     assert "unavailable" not in d, d
     assert d["value"] > 0 and d["cores"] >= 1 and d["unit"] == "GTEPS" and "OpenMP" in d["kind"]
     assert "source rows" in d["sample"]
+
+
+@pytest.mark.parametrize("pagerank", [True, False])
+def test_cpu_parallel_whole_graph_entry(pagerank):
+    sys.path.insert(0, ROOT)
+    import bench
+    import gen
+
+    g = gen.rmat(12, 8, seed=4, undirected=not pagerank)
+    d = bench.cpu_parallel_whole(g, pagerank)
+    assert "unavailable" not in d, d
+    assert d["value"] > 0 and d["cores"] >= 1 and "whole graph" in d["sample"]
