@@ -1,9 +1,9 @@
 """Mutation check of the oracle's pins: plausible mistakes are planted in copies of
 oracle/ipg_oracle.c (a dropped term, a wrong comparison or index, a transposed
 argument, a wrong combine), each copy is compiled on the CPU, and the CPU pin suites
-(closed forms, library routines, hand-worked examples) are run against it through
-IPG_ORACLE_LIB.  Every mutant must fail at least one pin; the unmodified source,
-built the same way, must pass them all."""
+(closed forms, library routines, hand-worked examples, random-graph properties) are run
+against it through IPG_ORACLE_LIB.  Every mutant must fail at least one pin; the
+unmodified source, built the same way, must pass them all."""
 import os
 import subprocess
 import sys
@@ -13,7 +13,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ipg_oracle.c")
-PIN_SUITES = ["tests/test_oracle_pins.py", "tests/test_oracle_pins_combiner.py", "tests/test_golden.py"]
+PIN_SUITES = ["tests/test_oracle_pins.py", "tests/test_oracle_pins_combiner.py", "tests/test_golden.py",
+              "tests/test_oracle_properties.py"]
 
 # (name, text in ipg_oracle.c, replacement, which occurrence (0-based), occurrences expected)
 MUTANTS = [
