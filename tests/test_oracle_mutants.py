@@ -46,6 +46,13 @@ MUTANTS = [
     ("combine: or instead of exclusive or", "orc_msg r = {(uint32_t)(x.a ^ y.a), 0};",
      "orc_msg r = {(uint32_t)(x.a | y.a), 0};", 0, 1),
     ("combine: 64-bit minimum keeps the maximum", "return x.a <= y.a ? x : y;", "return x.a >= y.a ? x : y;", 0, 1),
+    ("min mailbox keeps only the first message", "if (msg < mb->msg_next[dst]) mb->msg_next[dst] = msg;", ";",
+     0, 1),
+    ("sssp: the final superstep not counted", "        s++;\n        if (sent == 0) break;",
+     "        if (sent == 0) break;\n        s++;", 1, 4),
+    ("pagerank: one update too few", "for (s = 0; s <= updates; ++s) {", "for (s = 0; s + 1 <= updates; ++s) {",
+     0, 1),
+    ("hashmin: labels start at 0", "label[v] = v;", "label[v] = 0;", 0, 1),
 ]
 
 
