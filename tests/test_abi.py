@@ -160,3 +160,23 @@ def test_every_handle_entry_point_rejects_null(tmp_path, lib):
     assert r.returncode == 0, r.stderr[-2000:]
     seen, bad = r.stdout.strip().rsplit("\n", 1)[-1].split(" ", 1)
     assert int(seen) >= 20 and bad == "[]", r.stdout
+
+
+def test_no_cpu_fallback_without_a_gpu(lib):
+    """With no CUDA device the product path refuses to run (IPG_ECUDA), never computing on
+    the host instead: graph creation from valid host arrays and the host allocator."""
+    import numpy as np
+    import torch
+
+    import paper_2010_01542_gb300 as ipg
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    offsets = np.array([0, 1, 2], dtype=np.uint64)
+    cols = np.array([1, 0], dtype=np.uint32)
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_graph_create(offsets, cols, None, 2, 2, False)
+    assert e.value.status == ipg.IPG_ECUDA
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.host_empty(1 << 20, np.uint32)
+    assert e.value.status in (ipg.IPG_ECUDA, ipg.IPG_ENOMEM)
