@@ -48,13 +48,15 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["billion", "pagerank16", "hashmin20", "batch", "cc-batch", "serve"],
+    p.add_argument("--workload", choices=["billion", "pagerank16", "hashmin20", "batch", "cc-batch", "serve",
+                                          "combiner"],
                    default="billion",
                    help="billion: the default bench line; pagerank16: PageRank on directed R-MAT 16/16; "
                         "hashmin20: Hashmin components on undirected R-MAT 20/16; "
                         "batch: 256-source batched SSSP vs one at a time; "
                         "cc-batch: 64 uneven Hashmin graphs in one object vs one at a time; "
-                        "serve: Poisson stream of mixed queries on 32 resident graphs")
+                        "serve: Poisson stream of mixed queries on 32 resident graphs; "
+                        "combiner: wide-message programs and the combination step alone")
     p.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
     p.add_argument("--requests", type=int, default=10000, help="serve: measured requests (after 10%% warm-up)")
     p.add_argument("--batch-sources", type=int, default=256)
@@ -592,6 +594,102 @@ def run_batch(a):
     h.destroy()
 
 
+def run_combiner(a):
+    """The general (hybrid) combiner on one GPU, graph resident.
+    Programs with wide messages on a directed weighted R-MAT graph (default scale 22, EF 16),
+    from the max-out-degree vertex: the shortest-path tree ((distance, parent) messages) and
+    shortest-path counting ((level, count) messages), beside plain SSSP (32-bit min) on the
+    same graph; messages/s each, distances checked equal on the device.
+    The combination step alone (ipg_combine_dev): 2^26 messages to uniform random vertices
+    among 2^22 mailboxes, for every message kind; messages/s and streamed GB/s."""
+    import torch
+
+    import gen
+    import paper_2010_01542_gb300 as ipg
+
+    world, rank, local = dist_init(a)
+    ipg.load_library()
+    scale = a.scale if a.scale != 26 else 22
+    ef = a.edge_factor if a.edge_factor != 28 else 16
+    dg = gen.rmat_device(scale, ef, seed=a.seed, weighted=True, device=local)
+    n, m = dg.n, dg.m
+    stream = torch.cuda.Stream()
+    h = ipg.ipg_graph_create_dev(dg.offsets, dg.cols, dg.weights, n, m, True, stream=stream)
+    src = gen.max_out_degree_vertex(dg.to_host())
+    del dg
+    d0 = torch.empty(n, dtype=torch.int32, device="cuda")
+    d1 = torch.empty(n, dtype=torch.int32, device="cuda")
+    par = torch.empty(n, dtype=torch.int32, device="cuda")
+    lvl = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(n, dtype=torch.int64, device="cuda")
+    progs = {
+        "sssp_min_u32": lambda: ipg.ipg_sssp_dev(h, src, d0, stream=stream),
+        "sssp_tree_u64": lambda: ipg.ipg_sssp_tree_dev(h, src, d1, par, stream=stream),
+        "bfs_paths_u128": lambda: ipg.ipg_bfs_paths_dev(h, src, lvl, cnt, stream=stream),
+    }
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = {}
+    for name, run in progs.items():
+        for _ in range(max(a.warmup, 1)):
+            count, st = run()
+        msgs = sum(s.messages_sent for s in st)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = all_max(e0.elapsed_time(e1) / a.steps, world)
+        results[name] = {"ms": round(ms, 3), "supersteps": count, "messages": msgs,
+                         "gteps": round(msgs / (ms / 1e3) / 1e9, 2)}
+    same_dist = bool(torch.equal(d0, d1))
+    # the combination step alone
+    k, nm = 1 << 26, 1 << 22
+    rng = np.random.default_rng(a.seed)
+    dst = torch.from_numpy(rng.integers(0, nm, size=k).astype(np.uint32).view(np.int32)).cuda()
+    kinds = {"xor_u32": (ipg.IPG_COMBINE_XOR_U32, 4, 0), "min_u64": (ipg.IPG_COMBINE_MIN_U64, 8, 0),
+             "min_u64_native_atomic": (ipg.IPG_COMBINE_MIN_U64, 8, ipg.IPG_COMBINE_NATIVE),
+             "sum_u64": (ipg.IPG_COMBINE_SUM_U64, 8, 0), "mincount_u128": (ipg.IPG_COMBINE_MINCOUNT_U128, 16, 0)}
+    combine = {}
+    for name, (kind, size, opt) in kinds.items():
+        if size == 4:
+            msgs_t = torch.from_numpy(rng.integers(0, 1 << 32, size=k, dtype=np.uint64).astype(np.uint32)
+                                      .view(np.int32)).cuda()
+            mail = torch.zeros(nm, dtype=torch.int32, device="cuda")
+        elif size == 8:
+            msgs_t = torch.from_numpy(rng.integers(0, 1 << 62, size=k, dtype=np.int64)).cuda()
+            mail = torch.zeros(nm, dtype=torch.int64, device="cuda")
+        else:
+            keys = rng.integers(0, 3, size=k, dtype=np.int64)
+            msgs_t = torch.from_numpy(np.stack([keys, np.ones(k, dtype=np.int64)], axis=1)).cuda()
+            mail = torch.zeros((nm, 2), dtype=torch.int64, device="cuda")
+        flags = torch.zeros(nm, dtype=torch.int32, device="cuda")
+        for _ in range(max(a.warmup, 1)):
+            recv = ipg.ipg_combine_dev(kind, nm, dst, msgs_t, flags, mail, opt, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            ipg.ipg_combine_dev(kind, nm, dst, msgs_t, flags, mail, opt, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = all_max(e0.elapsed_time(e1) / a.steps, world)
+        combine[name] = {"ms": round(ms, 3), "g_messages_per_s": round(k / (ms / 1e3) / 1e9, 2),
+                         "streamed_gbs": round(k * (4 + size) / (ms / 1e3) / 1e9, 1), "receivers": recv}
+        del msgs_t, mail, flags
+    if rank == 0:
+        tree = results["sssp_tree_u64"]
+        line = {"metric": "GTEPS, shortest-path tree (hybrid combiner, 64-bit messages)", "unit": UNIT,
+                "value": round(world * tree["messages"] / (tree["ms"] / 1e3) / 1e9, 3), "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": tree["ms"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64/u128", "data": "synthetic",
+                "config": {"workload": f"rmat{scale}-ef{ef} directed weighted[1,255] seed {a.seed}, source = "
+                                       f"max-out-degree vertex; combine step: 2^26 messages into 2^22 mailboxes",
+                           "n": n, "m": m, "source": int(src)},
+                "programs": results, "tree_distances_equal_sssp": same_dist, "combine": combine}
+        print(json.dumps(line), flush=True)
+    h.destroy()
+
+
 def cc_batch_scales(count, seed):
     """scale_i = 10 + splitmix64(splitmix64(seed) + i) % 11: uneven graphs of 2^10 .. 2^20 vertices."""
     import gen
@@ -882,6 +980,8 @@ def main():
         run_cc_batch(a)
     elif a.workload == "serve":
         run_serve(a)
+    elif a.workload == "combiner":
+        run_combiner(a)
     else:
         run_ours(a)
 
