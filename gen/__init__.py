@@ -291,3 +291,30 @@ def rmat_device(scale: int, edge_factor: int, seed: int = 1, a: float = 0.57, b:
             lib.gen_rmat_cuda_free(plan)
     return DeviceCSR(n=n.value, m=m.value, offsets=offsets, cols=cols[:m.value],
                      weights=None if w is None else w[:m.value], directed=not undirected)
+
+
+# ---------------------------------------------------------------------------------------
+# Workload recipes: the seeded choices (graph sizes, query sources) of the batched and
+# served workloads, shared by bench.py and the tests that hold those workloads to the oracle.
+
+
+def _splitmix_draws(count: int, seed: int):
+    base = splitmix64(seed)
+    return [splitmix64((base + i) & 0xFFFFFFFFFFFFFFFF) for i in range(count)]
+
+
+def cc_batch_scales(count: int = 64, seed: int = 1):
+    """Many-graph Hashmin: scale_i = 10 + splitmix64(splitmix64(seed) + i) % 11 (2^10 .. 2^20
+    vertices), undirected, EF 16, graph seed i + 1."""
+    return [10 + d % 11 for d in _splitmix_draws(count, seed)]
+
+
+def serve_scales(count: int = 32, seed: int = 1):
+    """Served graph set: scale_i = 12 + splitmix64(splitmix64(seed) + i) % 11 (2^12 .. 2^22
+    vertices), undirected, weighted, EF 16, graph seed 101 + i."""
+    return [12 + d % 11 for d in _splitmix_draws(count, seed)]
+
+
+def batch_sources(n: int, k: int = 256, seed: int = 1) -> np.ndarray:
+    """Many-source SSSP: k sources uniform on [0, n) from numpy's PCG64 stream of `seed`."""
+    return np.random.default_rng(seed).integers(0, n, size=k).astype(np.uint32)

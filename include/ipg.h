@@ -255,10 +255,17 @@ ipg_status ipg_sssp_batch_dev(ipg_graph* g, const uint32_t* sources, uint32_t k,
  *   supersteps_out: optional, the Pregel superstep count;
  *   stream: cudaStream_t as void* (NULL = legacy default stream).
  * The first call on a device looks up the scratch array's device address (with
- * that device current); make that first call before any stream capture.  Every
- * call on a device shares the one scratch array and finds the previous call's
- * contents there (it clears what must start at zero): calls that overlap on the
- * GPU, from several streams or threads, race and give wrong results.
+ * that device current).  Under CUDA's default lazy module loading that lookup
+ * is also what loads this part of the library's device code onto the device and
+ * reserves the 16 MiB array, so the first call on each device does take device
+ * memory and can fail (IPG_ECUDA) when none is left; later calls take none.
+ * Callers on a fixed budget should therefore make one warm-up call at start-up
+ * (a one-vertex graph will do) while memory is still available.
+ * Every call on a device shares the one scratch array and finds the previous
+ * call's contents there (it clears what must start at zero): calls that overlap
+ * on the GPU, from several streams or threads, race and give wrong results.
+ * The call synchronizes `stream` once per superstep to read the frontier size,
+ * so it cannot be issued while that stream is being captured into a CUDA graph.
  */
 #define IPG_NOALLOC_MAX_VERTICES (1u << 20)
 ipg_status ipg_sssp_noalloc(const uint64_t* offsets_dev, const uint32_t* columns_dev, const uint32_t* weights_dev,
@@ -325,7 +332,14 @@ ipg_status ipg_bfs_paths_dev(ipg_graph* g, uint32_t source, uint32_t* level_dev,
  *   options    IPG_COMBINE_WARP (fold same-destination messages within a warp
  *              before the mailbox) and/or IPG_COMBINE_NATIVE (IPG_COMBINE_MIN_U64
  *              only: a hardware 64-bit atomicMin on a slot preset to the maximum
- *              instead of the hybrid combiner; same result — a comparison point).
+ *              instead of the hybrid combiner; same result — a comparison point);
+ *              IPG_COMBINE_STALLED (hybrid combiner only) starts every mailbox
+ *              CLAIMED by a first sender that never publishes — the state a
+ *              stalled writer would leave — and lets a send poll such a flag
+ *              only 64 times: every send's bounded wait runs out, no message is
+ *              delivered, flags_dev is left CLAIMED (2) and the call returns
+ *              IPG_ETIMEOUT within milliseconds.  It exercises the timeout path
+ *              of the combiner without any hang.
  * Returns after the result is complete on `stream`.  k may be 0.
  */
 typedef enum {
@@ -336,6 +350,7 @@ typedef enum {
 } ipg_combine_kind;
 #define IPG_COMBINE_WARP 1u
 #define IPG_COMBINE_NATIVE 2u
+#define IPG_COMBINE_STALLED 4u
 ipg_status ipg_combine_dev(int kind, uint32_t n, const uint32_t* dst_dev, const void* msgs_dev, uint64_t k,
                            uint32_t* flags_dev, void* mail_dev, uint64_t* receivers_out, uint32_t options,
                            void* stream);

@@ -168,9 +168,11 @@ __device__ __forceinline__ bool ipg_mail_cas_combine(Msg* slot, const Msg& m, un
 // Deliver m to the mailbox (flag, slot).  Returns 1 if it was the mailbox's first
 // message (the caller can record the receiver exactly once), 0 if it was combined
 // into an existing one, -1 if a bounded wait ran out (IPG_MAIL_STATUS_TIMEOUT is
-// raised in *status and the message is not delivered).
+// raised in *status and the message is not delivered).  spin_limit bounds the
+// polls of a CLAIMED flag (step 3).
 template <class Combine, class Msg>
-__device__ __forceinline__ int ipg_mail_send(unsigned int* flag, Msg* slot, const Msg& m, unsigned int* status) {
+__device__ __forceinline__ int ipg_mail_send(unsigned int* flag, Msg* slot, const Msg& m, unsigned int* status,
+                                             unsigned int spin_limit = IPG_MAIL_SPIN_LIMIT) {
     unsigned int f = ipg_mail::load_acquire(flag);
     if (f == IPG_MAIL_EMPTY) {
         if (atomicCAS(flag, IPG_MAIL_EMPTY, IPG_MAIL_CLAIMED) == IPG_MAIL_EMPTY) {
@@ -183,7 +185,7 @@ __device__ __forceinline__ int ipg_mail_send(unsigned int* flag, Msg* slot, cons
     if (f != IPG_MAIL_FULL) {
         unsigned int i = 0;
         do {
-            if (++i > IPG_MAIL_SPIN_LIMIT) {
+            if (++i > spin_limit) {
                 atomicOr(status, IPG_MAIL_STATUS_TIMEOUT);
                 return -1;
             }

@@ -496,6 +496,7 @@ __all__ += ["ipg_graph_create_batch", "ipg_graph_instances", "ipg_hashmin_cc_bat
 IPG_COMBINE_XOR_U32, IPG_COMBINE_MIN_U64, IPG_COMBINE_SUM_U64, IPG_COMBINE_MINCOUNT_U128 = 0, 1, 2, 3
 IPG_COMBINE_WARP = 1
 IPG_COMBINE_NATIVE = 2
+IPG_COMBINE_STALLED = 4
 _COMBINE_SIZE = {IPG_COMBINE_XOR_U32: 4, IPG_COMBINE_MIN_U64: 8, IPG_COMBINE_SUM_U64: 8, IPG_COMBINE_MINCOUNT_U128: 16}
 
 
@@ -568,7 +569,7 @@ def ipg_combine_dev(kind: int, n: int, dst_dev, msgs_dev, flags_dev, mail_dev, o
 
 __all__ += ["ipg_sssp_tree", "ipg_sssp_tree_dev", "ipg_bfs_paths", "ipg_bfs_paths_dev", "ipg_combine_dev",
             "IPG_COMBINE_XOR_U32", "IPG_COMBINE_MIN_U64", "IPG_COMBINE_SUM_U64", "IPG_COMBINE_MINCOUNT_U128",
-            "IPG_COMBINE_WARP", "IPG_COMBINE_NATIVE"]
+            "IPG_COMBINE_WARP", "IPG_COMBINE_NATIVE", "IPG_COMBINE_STALLED"]
 
 
 # ---------------------------------------------------------------------------------------

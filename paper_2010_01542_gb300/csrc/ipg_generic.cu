@@ -469,7 +469,7 @@ template <class Combine, class Msg, bool kWarp>
 __global__ void __launch_bounds__(kGenThreads) combine_kernel(const uint32_t* __restrict__ dst,
                                                                const Msg* __restrict__ msgs, uint64_t k, uint32_t n,
                                                                uint32_t* __restrict__ flag, Msg* __restrict__ mail,
-                                                               GenCounters* __restrict__ gc) {
+                                                               GenCounters* __restrict__ gc, unsigned int spin_limit) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     unsigned int first_count = 0;
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < k; base += stride) {
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kGenThreads) combine_kernel(const uint32_t* __
             const unsigned act = __ballot_sync(0xFFFFFFFFu, ok);
             if (ok) send = ipg_warp_combine<Combine>(act, v, &m);
         }
-        if (send && ipg_mail_send<Combine>(&flag[v], &mail[v], m, &gc->status) == 1) ++first_count;
+        if (send && ipg_mail_send<Combine>(&flag[v], &mail[v], m, &gc->status, spin_limit) == 1) ++first_count;
     }
     for (int o = 16; o > 0; o >>= 1) first_count += __shfl_down_sync(0xFFFFFFFFu, first_count, o);
     if ((threadIdx.x & 31) == 0 && first_count) atomicAdd(&gc->recv, first_count);
@@ -535,6 +535,11 @@ __global__ void preset_max_kernel(unsigned long long* __restrict__ mail, uint32_
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) mail[v] = ~0ull;
 }
 
+__global__ void fill_flags_kernel(uint32_t* __restrict__ flag, uint32_t n, uint32_t value) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) flag[v] = value;
+}
+
 __global__ void count_flags_kernel(const uint32_t* __restrict__ flag, uint32_t n, GenCounters* __restrict__ gc) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     unsigned int c = 0;
@@ -545,14 +550,17 @@ __global__ void count_flags_kernel(const uint32_t* __restrict__ flag, uint32_t n
 
 template <class Combine, class Msg>
 void launch_combine(bool warp, unsigned grid, cudaStream_t st, const uint32_t* dst, const void* msgs, uint64_t k,
-                    uint32_t n, uint32_t* flag, void* mail, GenCounters* gc) {
+                    uint32_t n, uint32_t* flag, void* mail, GenCounters* gc, unsigned spin_limit) {
     if (warp)
         combine_kernel<Combine, Msg, true><<<grid, kGenThreads, 0, st>>>(dst, static_cast<const Msg*>(msgs), k, n, flag,
-                                                                         static_cast<Msg*>(mail), gc);
+                                                                         static_cast<Msg*>(mail), gc, spin_limit);
     else
         combine_kernel<Combine, Msg, false><<<grid, kGenThreads, 0, st>>>(dst, static_cast<const Msg*>(msgs), k, n,
-                                                                          flag, static_cast<Msg*>(mail), gc);
+                                                                          flag, static_cast<Msg*>(mail), gc, spin_limit);
 }
+
+// polls of a CLAIMED flag allowed under IPG_COMBINE_STALLED before a send gives up
+constexpr unsigned kStalledSpinLimit = 64;
 
 struct MinCount128 {
     __device__ LevelCount operator()(const LevelCount& a, const LevelCount& b) const {
@@ -666,12 +674,16 @@ ipg_status ipg_combine_dev(int kind, uint32_t n, const uint32_t* dst_dev, const 
     const char* name = "ipg_combine_dev";
     if (kind < IPG_COMBINE_XOR_U32 || kind > IPG_COMBINE_MINCOUNT_U128)
         return set_error(IPG_EINVAL, "%s: unknown kind %d", name, kind);
-    if (options & ~(IPG_COMBINE_WARP | IPG_COMBINE_NATIVE))
+    if (options & ~(IPG_COMBINE_WARP | IPG_COMBINE_NATIVE | IPG_COMBINE_STALLED))
         return set_error(IPG_EINVAL, "%s: unknown option bits 0x%x", name, options);
     const bool native = options & IPG_COMBINE_NATIVE;
     const bool warp = options & IPG_COMBINE_WARP;
+    const bool stalled = options & IPG_COMBINE_STALLED;
     if (native && kind != IPG_COMBINE_MIN_U64)
         return set_error(IPG_EINVAL, "%s: IPG_COMBINE_NATIVE applies to IPG_COMBINE_MIN_U64 only", name);
+    if (native && stalled)
+        return set_error(IPG_EINVAL, "%s: IPG_COMBINE_STALLED applies to the hybrid combiner only", name);
+    const unsigned spin_limit = stalled ? kStalledSpinLimit : IPG_MAIL_SPIN_LIMIT;
     if (k && (!dst_dev || !msgs_dev)) return set_error(IPG_EINVAL, "%s: messages are NULL", name);
     if (n && (!flags_dev || !mail_dev)) return set_error(IPG_EINVAL, "%s: mailboxes are NULL", name);
     if (k && !n) return set_error(IPG_EINVAL, "%s: messages for an empty vertex set", name);
@@ -691,9 +703,16 @@ ipg_status ipg_combine_dev(int kind, uint32_t n, const uint32_t* dst_dev, const 
     GenCounters h{};
     do {
         if (cudaMemsetAsync(gc, 0, sizeof(GenCounters), st) != cudaSuccess ||
-            (n && cudaMemsetAsync(flags_dev, 0, sizeof(uint32_t) * n, st) != cudaSuccess)) {
+            (n && !stalled && cudaMemsetAsync(flags_dev, 0, sizeof(uint32_t) * n, st) != cudaSuccess)) {
             rc = set_error(IPG_ECUDA, "%s: memset failed", name);
             break;
+        }
+        if (n && stalled) {  // every mailbox held by a first sender that never publishes
+            fill_flags_kernel<<<grid_for(n, sms * 8), 256, 0, st>>>(flags_dev, n, IPG_MAIL_CLAIMED);
+            if (cudaGetLastError() != cudaSuccess) {
+                rc = set_error(IPG_ECUDA, "%s: kernel launch failed", name);
+                break;
+            }
         }
         const unsigned grid = grid_for(k, sms * 8);
         if (k) {
@@ -710,16 +729,18 @@ ipg_status ipg_combine_dev(int kind, uint32_t n, const uint32_t* dst_dev, const 
                 count_flags_kernel<<<grid_for(n, sms * 8), 256, 0, st>>>(flags_dev, n, gc);
             } else if (kind == IPG_COMBINE_XOR_U32) {
                 launch_combine<XorCombine<unsigned int>, unsigned int>(warp, grid, st, dst_dev, msgs_dev, k, n,
-                                                                       flags_dev, mail_dev, gc);
+                                                                       flags_dev, mail_dev, gc, spin_limit);
             } else if (kind == IPG_COMBINE_MIN_U64) {
                 launch_combine<MinCombine<unsigned long long>, unsigned long long>(warp, grid, st, dst_dev, msgs_dev,
-                                                                                   k, n, flags_dev, mail_dev, gc);
+                                                                                   k, n, flags_dev, mail_dev, gc,
+                                                                                   spin_limit);
             } else if (kind == IPG_COMBINE_SUM_U64) {
                 launch_combine<SumCombine<unsigned long long>, unsigned long long>(warp, grid, st, dst_dev, msgs_dev,
-                                                                                   k, n, flags_dev, mail_dev, gc);
+                                                                                   k, n, flags_dev, mail_dev, gc,
+                                                                                   spin_limit);
             } else {
                 launch_combine<MinCount128, LevelCount>(warp, grid, st, dst_dev, msgs_dev, k, n, flags_dev, mail_dev,
-                                                        gc);
+                                                        gc, spin_limit);
             }
             if (cudaGetLastError() != cudaSuccess) {
                 rc = set_error(IPG_ECUDA, "%s: kernel launch failed", name);

@@ -1,6 +1,7 @@
 // Graph object: device copy of the CSR, validation, the in-edge (CSC) copy for
 // pull-based supersteps, error reporting and small shared helpers.
 #include <stdarg.h>
+#include <atomic>
 #include <stdio.h>
 #include <string.h>
 
@@ -510,6 +511,20 @@ done:
 }
 
 int sm_count_of(int dev) { return device_sms(dev); }
+
+int sm_count_current() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return device_sms(0);
+    if (dev >= kMaxDev) return device_sms(dev);
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        v = device_sms(dev);
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
 
 __global__ void map_ids_kernel(const uint32_t* __restrict__ inv, uint32_t* __restrict__ ids, uint32_t k) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) ids[i] = inv[ids[i]];

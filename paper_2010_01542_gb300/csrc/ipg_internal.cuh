@@ -193,6 +193,8 @@ ipg_status ensure_pull_partition(ipg_graph* g, cudaStream_t st);
 ipg_status count_in_nonempty(ipg_graph* g, cudaStream_t st);
 ipg_status ensure_push_workspace(ipg_graph* g, bool receivers);
 int sm_count_of(int dev);
+// SMs of the current device (queried once per device and cached)
+int sm_count_current();
 // in ipg_graph.cu: shared by create and create_batch
 ipg_status create_graph(const uint64_t* offsets, const uint32_t* columns, const uint32_t* weights, uint32_t n,
                         uint64_t m, int directed, cudaStream_t user_stream, bool from_device, ipg_graph** out);

@@ -10,10 +10,12 @@
 // This entry point reads the caller's device CSR in place and keeps all of its
 // working state (visited stamps, two frontier lists, the frontier values and a few
 // counters) in one fixed array that lives in the library's own device image:
-// about 16 MiB, reserved on every GPU that loads the library and held until the
-// process exits.  It therefore handles at most IPG_NOALLOC_MAX_VERTICES vertices
-// and rejects larger graphs.  It calls no cudaMalloc, cudaFree or other
-// allocating routine.
+// about 16 MiB per GPU, held until the process exits.  With CUDA's lazy module
+// loading (the default) the array is reserved when this file's device code is
+// loaded onto a GPU, which the first call on that GPU triggers through its
+// cudaGetSymbolAddress; every later call takes no device memory.  It therefore
+// handles at most IPG_NOALLOC_MAX_VERTICES vertices and rejects larger graphs.
+// It calls no cudaMalloc, cudaFree or other allocating routine.
 //
 // The kernels are a simpler variant of the push superstep in ipg_push.cu: one warp
 // per frontier vertex instead of the merge-path split, with the same synchronous
@@ -138,7 +140,8 @@ __global__ void na_snapshot(const uint32_t* __restrict__ dist, const uint32_t* _
 unsigned na_grid(uint64_t threads) {
     uint64_t b = (threads + 255) / 256;
     if (b < 1) b = 1;
-    return (unsigned)(b < 152 * 8 ? b : 152 * 8);
+    const uint64_t cap = (uint64_t)sm_count_current() * 8;
+    return (unsigned)(b < cap ? b : cap);
 }
 
 }  // namespace

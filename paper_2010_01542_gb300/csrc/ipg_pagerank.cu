@@ -35,7 +35,8 @@ __global__ void mp_partition_kernel(const uint64_t* __restrict__ off, uint32_t n
     }
 }
 
-static unsigned grid_cap(uint64_t work, unsigned cap = 152 * 16) {
+static unsigned grid_cap(uint64_t work, unsigned cap = 0) {
+    if (!cap) cap = (unsigned)sm_count_current() * 16;
     uint64_t b = (work + 255) / 256;
     if (b < 1) b = 1;
     return (unsigned)(b < cap ? b : cap);

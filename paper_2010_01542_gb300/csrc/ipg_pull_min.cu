@@ -201,7 +201,8 @@ ipg_status launch_any(ipg_graph* g, bool sssp, bool recv, uint32_t* val, uint32_
 unsigned small_grid(uint64_t work) {
     uint64_t b = (work + 255) / 256;
     if (b < 1) b = 1;
-    return (unsigned)(b < 152 * 16 ? b : 152 * 16);
+    const uint64_t cap = (uint64_t)sm_count_current() * 16;
+    return (unsigned)(b < cap ? b : cap);
 }
 
 void launch_fixup(ipg_graph* g, bool recv, uint32_t* val, uint32_t* next0, uint32_t* next1, const PushLoop* loop,

@@ -427,7 +427,8 @@ __global__ void local_labels_kernel(uint32_t* __restrict__ labels, uint32_t n, c
         labels[v] -= bases[instance_of(bases, count, (uint32_t)v)];
 }
 
-unsigned grid_cap(uint64_t work, unsigned cap = 152 * 16) {
+unsigned grid_cap(uint64_t work, unsigned cap = 0) {
+    if (!cap) cap = (unsigned)sm_count_current() * 16;
     uint64_t b = (work + 255) / 256;
     if (b < 1) b = 1;
     return (unsigned)(b < cap ? b : cap);

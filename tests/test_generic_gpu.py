@@ -293,3 +293,44 @@ def test_combine_errors(ipg):
     flags.fill_(3)
     assert ipg.ipg_combine_dev(oracle.COMBINE_MIN_U64, n, d[:0], m[:0], flags, mail) == 0
     assert int(flags.sum()) == 0
+
+
+@pytest.mark.parametrize("kind", list(KINDS), ids=list(KINDS.values()))
+@pytest.mark.parametrize("options", [0, 1], ids=["mailbox", "warp"])
+def test_combiner_bounded_wait_runs_out(ipg, kind, options):
+    """Every mailbox starts CLAIMED by a first sender that never publishes (the state a
+    stalled writer leaves): each send's bounded wait must run out, the device raises its
+    timeout status and the call returns IPG_ETIMEOUT promptly, delivering nothing; the
+    library stays usable afterwards."""
+    import time
+
+    import torch
+
+    n, k = 1000, 1 << 16
+    dst, msgs = _messages(kind, n, k, seed=11, hot=0.2)
+    dt = torch.int32 if kind == oracle.COMBINE_XOR_U32 else torch.int64
+    d = torch.from_numpy(dst.view(np.int32)).cuda()
+    m = torch.from_numpy(msgs.view(np.int32 if dt == torch.int32 else np.int64)).cuda()
+    shape = (n, 2) if kind == oracle.COMBINE_MINCOUNT_U128 else (n,)
+    flags = torch.zeros(n, dtype=torch.int32, device="cuda")
+    mail = torch.full(shape, 5, dtype=dt, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_combine_dev(kind, n, d, m, flags, mail, options | ipg.IPG_COMBINE_STALLED)
+    elapsed = time.perf_counter() - t0
+    assert e.value.status == ipg.IPG_ETIMEOUT and "bounded wait" in str(e.value)
+    assert elapsed < 5.0, elapsed
+    assert (flags.cpu().numpy() == 2).all()  # still CLAIMED: nothing was published
+    assert (mail.cpu().numpy() == 5).all()   # no slot was written
+    # the same messages on ordinary empty mailboxes still combine exactly
+    ref = oracle.combine(kind, n, dst, msgs)
+    r, fl, ml = _gpu_combine(ipg, kind, n, dst, msgs, options)
+    assert r == ref.receivers
+    np.testing.assert_array_equal(ml[ref.has], ref.mail[ref.has])
+    m64 = torch.zeros(k, dtype=torch.int64, device="cuda")
+    mail64 = torch.zeros(n, dtype=torch.int64, device="cuda")
+    with pytest.raises(ipg.IpgError) as e:  # the hardware atomic has no wait to run out
+        ipg.ipg_combine_dev(oracle.COMBINE_MIN_U64, n, d, m64, flags, mail64,
+                            ipg.IPG_COMBINE_NATIVE | ipg.IPG_COMBINE_STALLED)
+    assert e.value.status == ipg.IPG_EINVAL

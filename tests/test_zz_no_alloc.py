@@ -1,13 +1,16 @@
 """ipg_sssp_noalloc, the SSSP entry point for callers that may not allocate device
 memory (their memory belongs to another allocator, or they run on a path where a
 cudaMalloc could stall or fail), returns the same distances and superstep count as
-ipg_sssp.  Its scratch is one fixed array that keeps the previous call's contents,
-so the check runs two calls in a row, and then a smaller graph after a larger one.
+ipg_sssp and as the CPU oracle.  Its scratch is one fixed array that keeps the previous
+call's contents, so the check runs two calls in a row, then a smaller graph after a
+larger one, and a graph of exactly the largest size the scratch holds.  After the first
+call on the device, a call must not change the device's free memory.
 Called through the C ABI; this file is collected last."""
 import numpy as np
 import pytest
 
 import gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +49,10 @@ def _compare(ipg, g, src, weighted=True):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(d.cpu().numpy().view(np.uint32), ref)
     assert steps == count
+    w = g.weights if weighted else None
+    o = oracle.sssp(g.n, g.offsets, g.cols, w, src)
+    np.testing.assert_array_equal(d.cpu().numpy().view(np.uint32), o.values)
+    assert steps == o.supersteps
 
 
 def test_noalloc_matches_ipg_sssp_on_consecutive_calls(ipg):
@@ -58,6 +65,31 @@ def test_noalloc_matches_ipg_sssp_on_consecutive_calls(ipg):
     small = gen.random_multigraph(300, 1500, seed=4, weighted=True)
     _compare(ipg, small, 0)  # a smaller graph after a larger one
     _compare(ipg, small, 299)
+
+
+def test_noalloc_at_its_vertex_limit(ipg):
+    """A graph of exactly IPG_NOALLOC_MAX_VERTICES vertices fills the scratch arrays."""
+    g = gen.rmat(20, 16, seed=22, weighted=True)
+    assert g.n == ipg.IPG_NOALLOC_MAX_VERTICES
+    _compare(ipg, g, gen.max_out_degree_vertex(g))
+    _compare(ipg, g, g.n - 1)  # the last vertex as the source
+    _compare(ipg, g, gen.max_out_degree_vertex(g), weighted=False)
+
+
+def test_noalloc_takes_no_device_memory_after_the_first_call(ipg):
+    import torch
+
+    g = gen.rmat(12, 16, seed=23, weighted=True)
+    offs, cols, w = _device_csr(g)
+    d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    ipg.ipg_sssp_noalloc(offs, cols, w, g.n, g.m, 0, d)  # the first call on this device
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for src in (0, 1, g.n - 1):
+        ipg.ipg_sssp_noalloc(offs, cols, w, g.n, g.m, src, d)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
 
 
 def test_noalloc_rejects_graphs_above_its_limit(ipg):
