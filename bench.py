@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--rate", type=float, default=2000.0, help="serve: mean arrivals per second")
     p.add_argument("--requests", type=int, default=10000, help="serve: measured requests (after 10%% warm-up)")
     p.add_argument("--batch-sources", type=int, default=256)
+    p.add_argument("--min-sssp-batch", type=int, default=0,
+                   help="serve: fewest queued SSSP queries that start a lane session (0: the library default)")
     p.add_argument("--scale", type=int, default=26)
     p.add_argument("--edge-factor", type=int, default=28)
     p.add_argument("--seed", type=int, default=1)
@@ -68,11 +70,24 @@ def parse():
                    help="calibration target for the oracle sample; the sample's SSSP part grows faster than "
                         "its size, so the measured time comes out at about half of it")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-other-configs", action="store_true",
+                   help="default run: skip the compact lines of the other workloads after the timed region")
     p.add_argument("--pull-divisor", type=int, default=None,
                    help="Hashmin/SSSP direction knob (library default if omitted; 0 = always push)")
     p.add_argument("--no-autotune", action="store_true",
                    help="skip ipg_autotune (the graph then runs with the process-wide knobs)")
     return p.parse_args()
+
+
+_CAPTURE = None  # a list while the default run collects the other workloads' lines
+
+
+def emit(line):
+    """Print a workload's JSON line, or keep it when the default run collects it."""
+    if _CAPTURE is not None:
+        _CAPTURE.append(line)
+    else:
+        print(json.dumps(line), flush=True)
 
 
 def workload_name(a):
@@ -184,32 +199,57 @@ class ClockSampler:
 # oracle sample (CPU baseline and the reference arm)
 
 
-def prefix_subgraph(g, edges):
-    """The first source rows of g holding about `edges` edges, over all n vertices."""
-    S = int(np.searchsorted(g.offsets, edges, side="right")) - 1
-    S = max(1, min(S, g.n))
-    mS = int(g.offsets[S])
-    off = g.offsets.copy()
-    off[S + 1:] = mS
-    return S, mS, off, g.cols[:mS], None if g.weights is None else g.weights[:mS]
+SAMPLE_BLOCK = 1024  # rows per sampled block
+
+
+def strided_subgraph(g, edges):
+    """A sample of g's source rows holding about `edges` edges, over all n vertices: blocks of
+    SAMPLE_BLOCK consecutive rows, one block in every `stride`.  R-MAT puts its hubs at the
+    lowest ids, so a prefix of rows would be all hubs; strided blocks take hub, middle and
+    tail rows in their proportions.  Returns (rows kept, edges kept, offsets, columns, weights,
+    description)."""
+    n, m = g.n, g.m
+    stride = max(1, int(round(m / max(edges, 1))))
+    deg = np.diff(g.offsets.astype(np.int64))
+    keep = (np.arange(n, dtype=np.int64) // SAMPLE_BLOCK) % stride == 0
+    deg_s = np.where(keep, deg, 0)
+    off = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(deg_s, out=off[1:])
+    starts = np.arange(0, n, SAMPLE_BLOCK * stride, dtype=np.int64)
+    ends = np.minimum(starts + SAMPLE_BLOCK, n)
+    pieces = [(int(g.offsets[b]), int(g.offsets[e])) for b, e in zip(starts, ends)]
+    cols = np.concatenate([g.cols[b:e] for b, e in pieces]) if pieces else g.cols[:0]
+    w = None if g.weights is None else np.concatenate([g.weights[b:e] for b, e in pieces])
+    rows = int(keep.sum())
+    desc = (f"{rows} source rows ({int(off[-1])} edges) in blocks of {SAMPLE_BLOCK} rows, one block in every "
+            f"{stride}, of the same graph, all n vertices")
+    return rows, int(off[-1]), off, cols, w, desc
+
+
+def sample_source(off, src):
+    """SSSP source in the sample: src if its row was kept, else the kept row of most out-edges."""
+    deg = np.diff(off.astype(np.int64))
+    return src if deg[src] > 0 else int(np.argmax(deg))
 
 
 def oracle_sample(g, src, edges):
-    """Oracle PageRank (one update) + SSSP on the row-prefix subgraph; returns (edges traversed, seconds)."""
+    """Oracle PageRank (one update) + SSSP on the strided row sample; returns (edges traversed,
+    seconds, description)."""
     import oracle
 
-    S, mS, off, cols, w = prefix_subgraph(g, edges)
+    _, _, off, cols, w, desc = strided_subgraph(g, edges)
+    s0 = sample_source(off, src)
     t0 = time.perf_counter()
     pr = oracle.pagerank(g.n, off, cols, 1)
-    ss = oracle.sssp(g.n, off, cols, w, src if src < S else 0)
+    ss = oracle.sssp(g.n, off, cols, w, s0)
     t = time.perf_counter() - t0
     traversed = sum(s.messages_sent for s in pr.stats) + sum(s.messages_sent for s in ss.stats)
-    return traversed, t, S, mS
+    return traversed, t, desc
 
 
 def calibrate_sample(g, src, seconds):
     edges = 20_000_000
-    tr, t, _, _ = oracle_sample(g, src, edges)
+    tr, t, _ = oracle_sample(g, src, edges)
     rate = tr / max(t, 1e-6)  # edges traversed per second
     per_edge = tr / max(edges, 1)
     return int(min(g.m, max(1_000_000, seconds * rate / max(per_edge, 1e-9))))
@@ -217,23 +257,24 @@ def calibrate_sample(g, src, seconds):
 
 def cpu_baseline(g, src, seconds):
     edges = calibrate_sample(g, src, seconds)
-    tr, t, S, mS = oracle_sample(g, src, edges)
+    tr, t, desc = oracle_sample(g, src, edges)
     return {"value": tr / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle PageRank (1 update) + SSSP to quiescence on the first {S} source rows "
-                      f"({mS} edges) of the same graph, all n vertices; {tr} edges traversed in {t:.1f} s"}
+            "sample": f"oracle PageRank (1 update) + SSSP to quiescence on {desc}; {tr} edges traversed "
+                      f"in {t:.1f} s"}
 
 
 def parallel_sample(g, src, edges):
-    """The OpenMP baseline (cpu_baseline/) on the same row-prefix subgraph as the oracle sample:
-    PageRank (one update, pull) + SSSP (push); returns (edges traversed, superstep seconds, S, mS)."""
+    """The OpenMP baseline (cpu_baseline/) on the same kind of strided row sample as the oracle's:
+    PageRank (one update, pull) + SSSP (push); returns (edges traversed, superstep seconds,
+    edges kept, wall seconds, description)."""
     import cpu_baseline as omp_baseline
 
-    S, mS, off, cols, w = prefix_subgraph(g, edges)
+    _, mS, off, cols, w, desc = strided_subgraph(g, edges)
     t0 = time.perf_counter()
     pr = omp_baseline.pagerank(g.n, off, cols, 1)
-    ss = omp_baseline.sssp(g.n, off, cols, w, src if src < S else 0)
+    ss = omp_baseline.sssp(g.n, off, cols, w, sample_source(off, src))
     wall = time.perf_counter() - t0  # also the untimed in-edge build: it sizes the sample
-    return pr.messages + ss.messages, pr.seconds + ss.seconds, S, mS, wall
+    return pr.messages + ss.messages, pr.seconds + ss.seconds, mS, wall, desc
 
 
 def cpu_parallel_baseline(g, src, seconds):
@@ -244,14 +285,14 @@ def cpu_parallel_baseline(g, src, seconds):
         import cpu_baseline as omp_baseline
 
         probe = 20_000_000
-        _, _, _, mS, wall = parallel_sample(g, src, probe)
+        _, _, mS, wall, _ = parallel_sample(g, src, probe)
         # size the sample so that its whole run (in-edge build + supersteps) takes about `seconds`
         edges = int(min(g.m, max(1_000_000, seconds * max(mS, 1) / max(wall, 1e-6))))
-        tr, t, S, mS, _ = parallel_sample(g, src, edges)
+        tr, t, mS, _, desc = parallel_sample(g, src, edges)
         return {"value": tr / t / 1e9, "unit": UNIT, "cores": omp_baseline.threads(),
                 "kind": "paper design: OpenMP, pull PageRank, push SSSP with CAS mailboxes, dynamic 256",
-                "sample": f"PageRank (1 update) + SSSP to quiescence on the first {S} source rows ({mS} edges) "
-                          f"of the same graph, all n vertices; {tr} edges traversed in {t:.2f} s of supersteps"}
+                "sample": f"PageRank (1 update) + SSSP to quiescence on {desc}; {tr} edges traversed in "
+                          f"{t:.2f} s of supersteps"}
     except Exception as e:  # noqa: BLE001 - a baseline must not take the bench down
         return {"unavailable": f"{type(e).__name__}: {e}"[:300]}
 
@@ -428,10 +469,12 @@ def run_ours(a):
         out_d = ipg.host_empty(n, np.uint32)
         times, e2e_edges = [], []
         phases = {"create": [], "pagerank": [], "sssp": [], "destroy": []}  # host calls return when done
+        create_parts = []
         for i in range(a.e2e_steps + 1):  # the first round is a warm-up
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             g2 = ipg.ipg_graph_create(host.offsets, host.cols, host.weights, n, m, True)
+            prof = ipg.ipg_graph_create_profile(g2)
             if tune:  # an identical graph: the tuning comes from the process-wide cache
                 ipg.ipg_autotune(g2, ipg.IPG_TUNE_PAGERANK | ipg.IPG_TUNE_SSSP, src)
             t1 = time.perf_counter()
@@ -447,11 +490,13 @@ def run_ours(a):
                 e2e_edges.append(pr_edges + statistics.mean(sssp_edges))
                 for k, v in zip(phases, (t1 - t0, t2 - t1, t3 - t2, t4 - t3)):
                     phases[k].append(v)
+                create_parts.append(prof)
         t_e2e = all_max(statistics.mean(times), world)
         e2e = {"value": round(world * statistics.mean(e2e_edges) / t_e2e / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": int(host.offsets.nbytes + host.cols.nbytes + host.weights.nbytes),
                "d2h_bytes_per_step": int(out_r.nbytes + out_d.nbytes), "ms_per_step": round(t_e2e * 1e3, 2),
                "phases_ms": {k: round(statistics.mean(v) * 1e3, 1) for k, v in phases.items()},
+               "create_ms": {k: round(statistics.mean(p[k] for p in create_parts), 1) for k in create_parts[0]},
                "api": "ipg_graph_create + ipg_autotune (cached) + ipg_pagerank + ipg_sssp + ipg_graph_destroy, "
                       "host buffers"}
 
@@ -460,14 +505,18 @@ def run_ours(a):
         cpu = cpu_baseline(host, src, a.cpu_seconds)
         cpu_par = cpu_parallel_baseline(host, src, 10.0)
 
+    l2_note = "inputs larger than L2 (graph %.1f GB resident)" % ((host.offsets.nbytes + 2 * host.cols.nbytes) / 1e9)
+    h.destroy()
+    del host
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": round(ms_max / a.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+u32", "data": "synthetic",
             "config": {"workload": workload_name(a), "scale": a.scale, "edge_factor": a.edge_factor, "n": n, "m": m,
-                       "sssp_source": src, "l2": "inputs larger than L2 (graph %.1f GB resident)" %
-                       ((host.offsets.nbytes + 2 * host.cols.nbytes) / 1e9),
+                       "sssp_source": src, "l2": l2_note,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "cpu_parallel": cpu_par, "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * a.steps)), "clocks": clocks,
@@ -483,17 +532,78 @@ def run_ours(a):
                      "gteps": round(statistics.mean(sssp_edges) / (statistics.mean(sssp_ms) / 1e3) / 1e9, 2),
                      "graph500_gteps": round(m / (statistics.mean(sssp_ms) / 1e3) / 1e9, 2)},  # m / run time
         }
-        print(json.dumps(line), flush=True)
-    h.destroy()
+        if world == 1 and not a.no_other_configs:
+            line["other_configs"] = run_other_configs(a)
+        emit(line)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
 
 
+def _compact(name, line):
+    if name in ("pagerank16", "hashmin20"):
+        r = line["roofline"]
+        return {"workload": line["config"]["workload"], "gteps": line["value"], "ms_per_step": line["ms_per_step"],
+                "roofline": {"kernel": r["kernel"], "achieved_gbs": r["achieved"], "frac": r["frac"]}}
+    if name in ("batch", "cc_batch"):
+        return {"workload": line["config"]["workload"], "unit": line["unit"], "value": line["value"],
+                "one_at_a_time": line["one_at_a_time"]["value"], "speedup": line["speedup"],
+                "results_equal": line["results_equal"]}
+    if name == "serve":
+        cb = line["continuous_batching"]
+        return {"workload": line["config"]["workload"], "offered_per_s": cb["offered_per_s"],
+                "queries_per_s": cb["queries_per_s"], "p50_ms": cb["p50_ms"], "p99_ms": cb["p99_ms"],
+                "joined_running_batch": cb.get("joined_running_batch"),
+                "one_at_a_time_queries_per_s": line["one_at_a_time"]["queries_per_s"],
+                "at_75pct_rate": {k: line["continuous_batching_at_75pct_rate"][k]
+                                  for k in ("queries_per_s", "p50_ms", "p99_ms")}}
+    c = line["combine"]
+    return {"workload": line["config"]["workload"],
+            "sssp_tree_u64_gteps": line["programs"]["sssp_tree_u64"]["gteps"],
+            "bfs_paths_u128_gteps": line["programs"]["bfs_paths_u128"]["gteps"],
+            "sssp_min_u32_gteps": line["programs"]["sssp_min_u32"]["gteps"],
+            "combine_g_messages_per_s": {k: v["g_messages_per_s"] for k, v in c.items() if isinstance(v, dict)},
+            "combine_call_overhead_ms": {k: v["call_overhead_ms"] for k, v in c.items() if isinstance(v, dict)}}
+
+
+def run_other_configs(a):
+    """The other workloads, each run once after the default run's timed region (never inside
+    it) with a few steps, reported as compact summaries; `bench.py --workload X` prints each
+    one's full line."""
+    global _CAPTURE
+    out = {}
+    jobs = (("pagerank16", lambda b: run_small_config(b, "pagerank16"), dict(steps=20, warmup=3)),
+            ("hashmin20", lambda b: run_small_config(b, "hashmin20"), dict(steps=20, warmup=3)),
+            ("batch", run_batch, dict(steps=3, warmup=1)),
+            ("cc_batch", run_cc_batch, dict(steps=5, warmup=2)),
+            ("serve", run_serve, dict(requests=6000)),
+            ("combiner", run_combiner, dict(steps=5, warmup=2)))
+    for name, fn, over in jobs:
+        b = argparse.Namespace(**vars(a))
+        b.no_cpu_baseline = True
+        for k, v in over.items():
+            setattr(b, k, v)
+        _CAPTURE = []
+        t0 = time.perf_counter()
+        try:
+            fn(b)
+            out[name] = _compact(name, _CAPTURE[-1]) if _CAPTURE else {"unavailable": "no line"}
+        except Exception as e:  # noqa: BLE001 - one workload must not take the headline line down
+            out[name] = {"unavailable": f"{type(e).__name__}: {e}"[:300]}
+        finally:
+            _CAPTURE = None
+        out[name]["seconds"] = round(time.perf_counter() - t0, 1)
+        import torch
+
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(a):
     """The oracle, as it stands, on the host cores: each step is a bounded sample of the
-    same workload (row-prefix subgraph, PageRank one update + SSSP)."""
+    same workload (strided row sample, PageRank one update + SSSP)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -514,11 +624,10 @@ def run_reference(a):
     trav, secs = 0, 0.0
     desc = None
     for _ in range(a.steps):
-        tr, t, S, mS = oracle_sample(g, src, edges)
+        tr, t, d = oracle_sample(g, src, edges)
         trav += tr
         secs += t
-        desc = (f"oracle PageRank (1 update) + SSSP to quiescence on the first {S} source rows ({mS} edges) "
-                f"of the same graph, all n vertices, 1 thread")
+        desc = f"oracle PageRank (1 update) + SSSP to quiescence on {d}, 1 thread"
     value = trav / secs / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(secs / a.steps * 1e3, 1),
@@ -527,7 +636,7 @@ def run_reference(a):
                                             "edge_factor": a.edge_factor, "n": g.n, "m": g.m},
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(line)
 
 
 def run_batch(a):
@@ -549,7 +658,7 @@ def run_batch(a):
     h = ipg.ipg_graph_create_dev(dg.offsets, dg.cols, dg.weights, n, m, True, stream=stream)
     del dg
     k = a.batch_sources
-    sources = np.random.default_rng(a.seed).integers(0, n, size=k).astype(np.uint32)
+    sources = gen.batch_sources(n, k, a.seed)
     out = torch.empty(k * n, dtype=torch.int32, device="cuda")
     single = torch.empty(n, dtype=torch.int32, device="cuda")
     for _ in range(max(a.warmup, 1)):
@@ -590,7 +699,7 @@ def run_batch(a):
                                   "ms_total": round(t_single, 2)},
                 "speedup": round(t_single / t_batch, 2), "results_equal": equal,
                 "supersteps": {"min": int(steps_b.min()), "max": int(steps_b.max())}}
-        print(json.dumps(line), flush=True)
+        emit(line)
     h.destroy()
 
 
@@ -673,8 +782,19 @@ def run_combiner(a):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = all_max(e0.elapsed_time(e1) / a.steps, world)
-        combine[name] = {"ms": round(ms, 3), "g_messages_per_s": round(k / (ms / 1e3) / 1e9, 2),
-                         "streamed_gbs": round(k * (4 + size) / (ms / 1e3) / 1e9, 1), "receivers": recv}
+        # the call's fixed cost (counter allocation, the flag clear, the copy back and the
+        # host synchronisation), timed as a call with no messages and the same options
+        e0.record(stream)
+        for _ in range(a.steps):
+            ipg.ipg_combine_dev(kind, nm, dst[:0], msgs_t[:0], flags, mail, opt, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fixed = all_max(e0.elapsed_time(e1) / a.steps, world)
+        net = max(ms - fixed, 1e-6)
+        combine[name] = {"ms": round(ms, 3), "call_overhead_ms": round(fixed, 3),
+                         "g_messages_per_s": round(k / (net / 1e3) / 1e9, 2),
+                         "g_messages_per_s_whole_call": round(k / (ms / 1e3) / 1e9, 2),
+                         "streamed_gbs": round(k * (4 + size) / (net / 1e3) / 1e9, 1), "receivers": recv}
         del msgs_t, mail, flags
     if rank == 0:
         tree = results["sssp_tree_u64"]
@@ -686,16 +806,8 @@ def run_combiner(a):
                                        f"max-out-degree vertex; combine step: 2^26 messages into 2^22 mailboxes",
                            "n": n, "m": m, "source": int(src)},
                 "programs": results, "tree_distances_equal_sssp": same_dist, "combine": combine}
-        print(json.dumps(line), flush=True)
+        emit(line)
     h.destroy()
-
-
-def cc_batch_scales(count, seed):
-    """scale_i = 10 + splitmix64(splitmix64(seed) + i) % 11: uneven graphs of 2^10 .. 2^20 vertices."""
-    import gen
-
-    base = gen.splitmix64(seed)
-    return [10 + gen.splitmix64((base + i) & 0xFFFFFFFFFFFFFFFF) % 11 for i in range(count)]
 
 
 def run_small_config(a, kind):
@@ -804,7 +916,7 @@ def run_small_config(a, kind):
                 "gpu_launches": ((1 + 2 * PR_UPDATES + 1) if pr else
                                  (1 + 5 * sum(1 for s in st if s.senders) + 1)) * a.steps,
                 "messages_per_superstep": [s.messages_sent for s in st]}
-        print(json.dumps(line), flush=True)
+        emit(line)
     h.destroy()
 
 
@@ -819,7 +931,7 @@ def run_cc_batch(a, count=64):
 
     world, rank, local = dist_init(a)
     ipg.load_library()
-    scales = cc_batch_scales(count, a.seed)
+    scales = gen.cc_batch_scales(count, a.seed)
     graphs = [gen.rmat_device(sc, 16, seed=i + 1, undirected=True, device=local).to_host()
               for i, sc in enumerate(scales)]
     hb = ipg.ipg_graph_create_batch(graphs, directed=False)
@@ -862,7 +974,7 @@ def run_cc_batch(a, count=64):
                                   "ms_total": round(t_single, 2)},
                 "speedup": round(t_single / t_batch, 2), "results_equal": equal,
                 "gteps": round(sum(int(x) for x in [total_m]) / (t_batch / 1e3) / 1e9, 2)}
-        print(json.dumps(line), flush=True)
+        emit(line)
 
 
 def serve_stream(srv, graphs, requests, rate, seed, warm):
@@ -888,7 +1000,7 @@ def serve_stream(srv, graphs, requests, rate, seed, warm):
             free[gi].append(slot)
             if c.status != 0:
                 raise RuntimeError(f"query {c.user} failed with status {c.status}")
-            recs[c.user] = (t_arr, c.t_done, kind, c.batch)
+            recs[c.user] = (t_arr, c.t_done, kind, c.batch, c.joined)
 
     t0 = srv.now() + 0.05
     for i in range(total):
@@ -912,14 +1024,16 @@ def serve_stream(srv, graphs, requests, rate, seed, warm):
 
 
 def serve_summary(recs):
-    lat = np.array([(d - a) * 1e3 for a, d, _, _ in recs.values()])
-    t_first = min(a for a, _, _, _ in recs.values())
-    t_last = max(d for _, d, _, _ in recs.values())
-    batches = np.array([b for _, _, k, b in recs.values() if k == 0])
-    shared = np.array([b for _, _, k, b in recs.values() if k != 0])
+    lat = np.array([(r[1] - r[0]) * 1e3 for r in recs.values()])
+    t_first = min(r[0] for r in recs.values())
+    t_last = max(r[1] for r in recs.values())
+    sssp = [r for r in recs.values() if r[2] == 0]
+    batches = np.array([r[3] for r in sssp])
+    shared = np.array([r[3] for r in recs.values() if r[2] != 0])
     return {"queries_per_s": round(len(recs) / (t_last - t_first), 1), "p50_ms": round(float(np.percentile(lat, 50)), 3),
             "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
             "sssp_batch_mean": round(float(batches.mean()), 2) if batches.size else None,
+            "joined_running_batch": int(sum(r[4] for r in sssp)), "sssp_queries": len(sssp),
             "cc_pr_shared_run_mean": round(float(shared.mean()), 2) if shared.size else None}
 
 
@@ -935,17 +1049,19 @@ def run_serve(a, count=32):
 
     world, rank, local = dist_init(a)
     ipg.load_library()
-    base = gen.splitmix64(a.seed)
-    scales = [12 + gen.splitmix64((base + i) & 0xFFFFFFFFFFFFFFFF) % 11 for i in range(count)]
+    scales = gen.serve_scales(count, a.seed)
     graphs = [gen.rmat_device(sc, 16, seed=101 + i, undirected=True, weighted=True, device=local).to_host()
               for i, sc in enumerate(scales)]
     handles = [ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, False) for g in graphs]
     warm = max(a.requests // 10, 100)
     res = {}
     # every server prepares the graphs' workspaces before the stream starts
-    for name, kw, rate in (("continuous_batching", dict(workers=8, max_batch=256, prepare=True), a.rate),
+    msb = a.min_sssp_batch
+    for name, kw, rate in (("continuous_batching", dict(workers=8, max_batch=256, prepare=True, min_sssp_batch=msb),
+                            a.rate),
                            ("one_at_a_time", dict(workers=1, max_batch=1, prepare=True), a.rate),
-                           ("continuous_batching_at_75pct_rate", dict(workers=8, max_batch=256, prepare=True),
+                           ("continuous_batching_at_75pct_rate",
+                            dict(workers=8, max_batch=256, prepare=True, min_sssp_batch=msb),
                             0.75 * a.rate)):
         srv = ipg.Server(handles, **kw)
         recs = serve_stream(srv, graphs, a.requests, rate, a.seed, warm)
@@ -965,7 +1081,7 @@ def run_serve(a, count=32):
                 "p50_ms": cb["p50_ms"], "p99_ms": cb["p99_ms"], "continuous_batching": cb,
                 "one_at_a_time": res["one_at_a_time"],
                 "continuous_batching_at_75pct_rate": res["continuous_batching_at_75pct_rate"]}
-        print(json.dumps(line), flush=True)
+        emit(line)
 
 
 def main():

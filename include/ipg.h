@@ -136,6 +136,24 @@ void ipg_graph_destroy(ipg_graph* g);
 ipg_status ipg_graph_info(const ipg_graph* g, uint32_t* n, uint64_t* m, int* directed, int* weighted);
 
 /*
+ * Where ipg_graph_create / _dev spent its time (a measurement aid; not in the
+ * paper).  Milliseconds:
+ *   alloc_ms         host wall time of the device allocations and the stream;
+ *   upload_issue_ms  host wall time to issue the three copies (pageable host
+ *                    memory makes this the whole copy; page-locked returns at once);
+ *   upload_ms        device time of the copies (CUDA events on the copy stream);
+ *   validate_ms      device time of the CSR checks;
+ *   renumber_ms      host wall time of the degree renumbering (sorts, row renaming,
+ *                    weight narrowing), including its waits;
+ *   total_ms         host wall time of the whole call.
+ * In-edge (CSC) building is not part of creation: it happens on first use.
+ */
+typedef struct {
+    float alloc_ms, upload_issue_ms, upload_ms, validate_ms, renumber_ms, total_ms;
+} ipg_create_profile;
+ipg_status ipg_graph_create_profile(const ipg_graph* g, ipg_create_profile* out);
+
+/*
  * ipg_graph_check_symmetric — does the stored graph equal its reverse?
  *   symmetric  out: 1 if the multiset of stored edges (u, v, w) equals the
  *              multiset of their reverses (v, u, w) (w omitted for an
@@ -389,8 +407,11 @@ typedef struct {
     uint64_t user;
     ipg_status status;
     uint32_t supersteps;  /* superstep count of the query's run */
-    uint32_t batch;       /* queries dispatched together with this one (itself included) */
-    uint32_t reserved;
+    uint32_t batch;       /* queries dispatched together with this one (itself included); for an
+                             SSSP query of a lane session: the session's queries on the device
+                             once it was seeded */
+    uint32_t joined;      /* 1: an SSSP query seeded into a lane session that was already running,
+                             at a superstep boundary (continuous batching); else 0 */
     double t_submit;      /* seconds on the server clock (ipg_server_now) */
     double t_start;
     double t_done;

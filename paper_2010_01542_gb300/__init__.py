@@ -21,7 +21,7 @@ from ._build import library_path
 
 __all__ = [
     "IpgError", "IpgLibraryMissing", "SuperstepStats", "Graph", "ipg_graph_create", "ipg_graph_create_dev",
-    "ipg_graph_destroy", "ipg_graph_info", "ipg_pagerank", "ipg_pagerank_dev", "ipg_hashmin_cc",
+    "ipg_graph_destroy", "ipg_graph_info", "ipg_graph_create_profile", "ipg_pagerank", "ipg_pagerank_dev", "ipg_hashmin_cc",
     "ipg_hashmin_cc_dev", "ipg_sssp", "ipg_sssp_dev", "ipg_last_error", "ipg_version",
     "IPG_STAT_RECEIVERS", "IPG_STAT_TIMING", "IPG_STAT_PULL", "INF", "load_library",
 ]
@@ -201,6 +201,21 @@ def ipg_graph_create_dev(offsets, columns, weights, n: int, m: int, directed: bo
 
 def ipg_graph_destroy(g: Graph) -> None:
     g.destroy()
+
+
+class _CCreateProfile(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("alloc_ms", "upload_issue_ms", "upload_ms", "validate_ms", "renumber_ms",
+                                             "total_ms")]
+
+
+def ipg_graph_create_profile(g: "Graph") -> dict:
+    """Where ipg_graph_create spent its time, in milliseconds (see include/ipg.h)."""
+    fn = load_library().ipg_graph_create_profile
+    fn.argtypes = [ctypes.c_void_p, ctypes.POINTER(_CCreateProfile)]
+    fn.restype = ctypes.c_int
+    p = _CCreateProfile()
+    _check(fn(g.handle, ctypes.byref(p)))
+    return {k: round(float(getattr(p, k)), 3) for k, _ in _CCreateProfile._fields_}
 
 
 def ipg_graph_info(g: Graph):
@@ -585,7 +600,7 @@ class _CQuery(ctypes.Structure):
 
 class _CCompletion(ctypes.Structure):
     _fields_ = [("user", ctypes.c_uint64), ("status", ctypes.c_int), ("supersteps", ctypes.c_uint32),
-                ("batch", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("t_submit", ctypes.c_double),
+                ("batch", ctypes.c_uint32), ("joined", ctypes.c_uint32), ("t_submit", ctypes.c_double),
                 ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
@@ -608,6 +623,7 @@ class Completion:
     t_start: float
     t_done: float
     out: Optional[np.ndarray] = None
+    joined: int = 0  # 1: an SSSP query that joined a lane session already running on the device
 
 
 class Server:
@@ -659,7 +675,8 @@ class Server:
         res = []
         for c in self._buf[:k]:
             res.append(Completion(int(c.user), int(c.status), int(c.supersteps), int(c.batch), float(c.t_submit),
-                                  float(c.t_start), float(c.t_done), self._outs.pop(int(c.user), None)))
+                                  float(c.t_start), float(c.t_done), self._outs.pop(int(c.user), None),
+                                  int(c.joined)))
         return res
 
     def cancel(self, user: int) -> int:

@@ -1,41 +1,53 @@
 // Batched SSSP: many sources on one graph, each an independent synchronous
 // Pregel SSSP (Sec. VI-C), run together superstep by superstep.
 //
-// Sources are processed in groups of 32, one per warp lane.  Values live
-// vertex-major, dist[v][lane], so the 32 sources' values of a vertex are one
-// 128-byte line: in a pull superstep every in-edge (u -> v) costs one coalesced
-// line read of u's sender values for all 32 sources, where 32 separate runs would
-// each pay a random 4-byte gather.  A superstep:
+// The engine has 32 lanes, one per warp lane; each lane holds one query (a
+// source) or is free.  Values live vertex-major, dist[v][lane], so the 32
+// lanes' values of a vertex are one 128-byte line: in a pull superstep every
+// in-edge (u -> v) costs one read of u's sender values for the lanes that send
+// from u (only their sectors of the line), where 32 separate runs would each pay
+// a random 4-byte gather.  A superstep:
+//   refill   free lanes take the next queries (from a device list of sources, or
+//            from seeds the host wrote at a superstep boundary): the source's
+//            value becomes 0 and it joins the current senders;
 //   pull     warps walk contiguous chunks of the in-edge lists (CSC).  Lane b keeps
 //            a running min of sval[u][b] + w over the current destination's edges
 //            and flushes it with atomicMin into dist[v][b] when the destination
 //            changes (a row split across chunks is finished by the atomics).  A
 //            lane whose atomicMin lowered the value marks v in cmask[v]; the first
-//            marker appends v to the next frontier (union over the 32 sources).
+//            marker appends v to the next frontier (union over the lanes);
 //   apply    the previous senders' snapshot rows are reset to kInf, and every
-//            vertex of the next frontier publishes dist[v][b] for the sources
+//            vertex of the next frontier publishes dist[v][b] for the lanes
 //            whose value dropped (kInf for the others), which is the snapshot the
-//            next superstep reads; per-source message counts (sum of the senders'
-//            out-degrees) come out of the same pass.
-// Senders therefore send the value they had at the start of the superstep, as in
-// the synchronous model, and every source's distances and superstep count equal
-// those of a standalone ipg_sssp run.
+//            next superstep reads; per-lane message counts (sum of the senders'
+//            out-degrees) come out of the same pass;
+//   step     a lane whose next senders send nothing has finished its query: its
+//            superstep count is final and the lane is marked for harvest;
+//   harvest  finished lanes' distances go to their output rows (in caller ids)
+//            and their columns are reset to kInf, which frees the lanes for the
+//            next refill.
+// Senders send the value they had at the start of the superstep, as in the
+// synchronous model; lanes never share values, so a query's distances and
+// superstep count equal those of a standalone ipg_sssp run whichever superstep
+// it joined at.
 //
 // A sparse superstep runs in push form instead: a task pass cuts the senders'
 // out-edge lists into tasks of kPushChunk edges, and a warp per task sends
 // sval[u][b] + w along each out-edge (u -> v) with atomicMin into dist[v][b].
 // Push and pull take the minimum of the same messages and mark the same
-// lowered lanes, so they are interchangeable; the step kernel picks push when
-// the senders' out-edges (summed by the apply pass) are fewer than m / divisor.
+// lowered lanes, so they are interchangeable; the refill kernel picks push when
+// the senders' out-edges are fewer than m / divisor.
 //
 // The superstep loop runs on the device: a CUDA graph holds a conditional WHILE
-// node whose body is one superstep (pull, reset, apply, step).  The kernels read
-// the frontier from a device control block, so their launch parameters never
-// change, and the step kernel decides whether another superstep follows.  One
-// graph launch runs at most kLoopCap supersteps; the host reads the control
-// block after each launch and relaunches while supersteps remain, so a group
-// costs a few host synchronisations instead of two per superstep, and no launch
-// can loop without bound.
+// node whose body is one superstep (refill, tasks, pull, push, reset, apply,
+// step, harvest).  The kernels read the frontier and the lanes from a device
+// control block, so their launch parameters never change, and the step kernel
+// decides whether another superstep follows.  ipg_sssp_batch keeps all 32 lanes
+// busy from its source list inside the loop, so k sources run in one graph launch
+// (plus one per kLoopCap supersteps).  The server seeds lanes itself: its launches
+// end at the first superstep where a lane finished, or when queries wait for a
+// free lane (a flag in mapped host memory), so queries join a running batch at
+// the next superstep boundary.
 #include "ipg_internal.cuh"
 
 namespace ipg {
@@ -43,31 +55,55 @@ namespace {
 
 constexpr int kLanes = 32;
 constexpr uint32_t kChunk = 256;  // in-edges per warp task
-constexpr int kUnroll = 4;         // sender lines in flight per warp
+#ifndef IPG_BATCH_UNROLL
+#define IPG_BATCH_UNROLL 4
+#endif
+constexpr int kUnroll = IPG_BATCH_UNROLL;  // sender lines in flight per warp
 
-constexpr unsigned kLoopCap = 64;      // supersteps per graph launch
+constexpr unsigned kLoopCap = 1024;    // supersteps per graph launch
 constexpr uint32_t kPushChunk = 256;   // out-edges per push task
 
 struct BatchCounters {
-    unsigned long long msgs[kLanes];  // messages the next superstep's senders send, per source
-    unsigned long long edges;         // out-edges of the next senders (union over sources)
+    unsigned long long msgs[kLanes];  // messages the next superstep's senders send, per lane
+    unsigned long long edges;         // out-edges of the next senders (union over lanes)
     unsigned int next_size;
     unsigned int status;
     unsigned int ntasks;              // push tasks of the current senders (push supersteps)
     unsigned int pad[11];
 };
 
-// device-resident loop state of one group
+}  // namespace
+
+// device-resident loop and lane state of one graph's batched engine
 struct BatchCtl {
     unsigned int cur;     // frontier buffer holding the current senders
     unsigned int f;       // current senders
     unsigned int iter;    // supersteps run by the current graph launch
-    unsigned int done;    // 1: no superstep left
+    unsigned int done;    // 1: no lane holds a query and none is left to take
     unsigned int status;  // kStatus* bits
     unsigned int push;    // 1: the current superstep runs in push form
     unsigned long long divisor;  // push when the senders' out-edges * divisor < m (0: always pull)
-    unsigned int count[kLanes];  // supersteps of each source's Pregel run
+    unsigned long long f_edges;  // out-edges of the current senders (union over lanes)
+    unsigned int live;           // lanes holding a query
+    unsigned int finished;       // lanes whose query ended in the last superstep
+    unsigned int count[kLanes];  // supersteps of each lane's query so far (final once finished)
+    unsigned int row[kLanes];    // output row of each lane's query
+    // refill from a device list (ipg_sssp_batch): caller ids, nqueries entries
+    unsigned int next_query, nqueries;
+    const uint32_t* src_list;
+    uint32_t* steps_out;  // per query: its superstep count (device), or NULL
+    // refill by the host (serving)
+    const volatile unsigned int* admit;  // mapped host flag: queries wait for a free lane (or NULL)
+    unsigned int stop_on_finish;         // end a graph launch after a superstep in which a lane finished
+    unsigned int nseed;                  // seeds below, taken by the next refill
+    unsigned int seed_src[kLanes];       // caller ids
+    unsigned int seed_row[kLanes];
+    // output: rows of n distances in caller order
+    uint32_t* out;
+    unsigned long long out_stride;
 };
+
+namespace {
 
 __device__ __forceinline__ uint32_t* fr_cur(uint32_t* fr0, uint32_t* fr1, const BatchCtl* ctl) {
     return ctl->cur ? fr1 : fr0;
@@ -96,22 +132,64 @@ __global__ void chunk_rows_kernel(const uint64_t* __restrict__ off, uint32_t n, 
     }
 }
 
-__global__ void batch_seed_kernel(const uint32_t* __restrict__ src_int, uint32_t k, const uint64_t* __restrict__ off,
-                                  uint32_t* __restrict__ dist, uint32_t* __restrict__ sval,
-                                  uint32_t* __restrict__ smask, uint32_t* __restrict__ frontier,
-                                  BatchCounters* __restrict__ ctr) {
+__device__ __forceinline__ bool batch_push_pick(unsigned long long edges, unsigned long long divisor, uint64_t m) {
+    return divisor > 0 && (double)edges * (double)divisor < (double)m;
+}
+
+// Free lanes take the next queries, in lane order: from the device source list,
+// or from the host's seeds.  The source's value becomes 0 and it joins the
+// current senders; its count starts at 1 (superstep 0), 2 if it has out-edges
+// (its messages make a superstep 1).  Then the superstep's form is picked.
+__global__ void batch_refill_kernel(BatchCtl* __restrict__ ctl, const uint32_t* __restrict__ inv,
+                                    const uint64_t* __restrict__ off, uint64_t m, uint32_t* __restrict__ dist,
+                                    uint32_t* __restrict__ sval, uint32_t* __restrict__ smask, uint32_t* fr0,
+                                    uint32_t* fr1) {
     const uint32_t b = threadIdx.x;
-    if (b < k) {
-        const uint32_t v = src_int[b];
+    const uint32_t live = ctl->live;
+    const bool is_free = !((live >> b) & 1u);
+    const unsigned freem = __ballot_sync(0xFFFFFFFFu, is_free);
+    const uint32_t rank = __popc(freem & ((1u << b) - 1u));
+    const bool from_list = ctl->nqueries != 0;
+    bool take = false;
+    uint32_t src = 0, row = 0;
+    if (from_list) {
+        const uint32_t q = ctl->next_query + rank;
+        take = is_free && q < ctl->nqueries;
+        if (take) {
+            src = ctl->src_list[q];
+            row = q;
+        }
+    } else {
+        take = is_free && rank < ctl->nseed;
+        if (take) {
+            src = ctl->seed_src[rank];
+            row = ctl->seed_row[rank];
+        }
+    }
+    const unsigned takem = __ballot_sync(0xFFFFFFFFu, take);
+    unsigned long long add = 0;
+    if (take) {
+        const uint32_t v = inv[src];
         dist[(uint64_t)v * kLanes + b] = 0;
         sval[(uint64_t)v * kLanes + b] = 0;
-        const unsigned old = atomicOr(&smask[v], 1u << b);
         const uint64_t deg = off[v + 1] - off[v];
-        if (old == 0) {
-            frontier[atomicAdd(&ctr->next_size, 1u)] = v;
-            atomicAdd(&ctr->edges, (unsigned long long)deg);
+        if (atomicOr(&smask[v], 1u << b) == 0) {
+            fr_cur(fr0, fr1, ctl)[atomicAdd(&ctl->f, 1u)] = v;
+            add = deg;
         }
-        ctr->msgs[b] = deg;
+        ctl->count[b] = 1u + (deg > 0 ? 1u : 0u);
+        ctl->row[b] = row;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) add += __shfl_down_sync(0xFFFFFFFFu, add, o);
+    if (b == 0) {
+        ctl->live = live | takem;
+        if (from_list)
+            ctl->next_query += __popc(takem);
+        else
+            ctl->nseed = 0;
+        ctl->f_edges += add;
+        ctl->push = batch_push_pick(ctl->f_edges, ctl->divisor, m);
     }
 }
 
@@ -180,8 +258,10 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
                         if (active) active &= active - 1;
                         const uint32_t u = __shfl_sync(0xFFFFFFFFu, u_l, jj);
                         const uint32_t w = __shfl_sync(0xFFFFFFFFu, w_l, jj);
+                        const uint32_t sm = __shfl_sync(0xFFFFFFFFu, sm_l, jj);
                         lim[q] = kInf - w;  // s + w stays below kInf iff s < lim
-                        s[q] = ok ? __ldg(sval + ((uint64_t)u * kLanes + lane)) : kInf;
+                        // only lanes whose source sends from u load: the line's other sectors stay untouched
+                        s[q] = ok && ((sm >> lane) & 1u) ? __ldg(sval + ((uint64_t)u * kLanes + lane)) : kInf;
                     }
 #pragma unroll
                     for (int q = 0; q < kUnroll; ++q) {
@@ -206,8 +286,9 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
                     const int src_lane = jj[q] < 0 ? 0 : jj[q];
                     const uint32_t u = __shfl_sync(0xFFFFFFFFu, u_l, src_lane);
                     const uint32_t w = __shfl_sync(0xFFFFFFFFu, w_l, src_lane);
+                    const uint32_t sm = __shfl_sync(0xFFFFFFFFu, sm_l, src_lane);
                     lim[q] = kInf - w;
-                    s[q] = jj[q] >= 0 ? __ldg(sval + ((uint64_t)u * kLanes + lane)) : kInf;  // one 128-byte line
+                    s[q] = jj[q] >= 0 && ((sm >> lane) & 1u) ? __ldg(sval + ((uint64_t)u * kLanes + lane)) : kInf;
                 }
 #pragma unroll
                 for (int q = 0; q < kUnroll; ++q) {
@@ -324,7 +405,8 @@ __global__ void __launch_bounds__(256) batch_push_kernel(
             }
             continue;
         }
-        const uint32_t s = sval[(uint64_t)u * kLanes + lane];  // kInf: lane b does not send from u
+        // kInf: lane b does not send from u (its sector is not loaded)
+        const uint32_t s = (senders >> lane) & 1u ? sval[(uint64_t)u * kLanes + lane] : kInf;
         for (uint64_t j0 = e_beg; j0 < e_end; j0 += 32) {
             const uint32_t cnt = (uint32_t)min((uint64_t)32, e_end - j0);
             uint32_t v_l = 0, w_l = 1;
@@ -395,46 +477,27 @@ __global__ void batch_apply_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl*
     if (lane == 0 && edges) atomicAdd(&ctr->edges, edges);
 }
 
-// the group's loop state after the seed: superstep 0 counts for every source,
-// superstep 1 for those whose source has out-edges
-__device__ __forceinline__ bool batch_push_pick(unsigned long long edges, unsigned long long divisor, uint64_t m) {
-    return divisor > 0 && (double)edges * (double)divisor < (double)m;
-}
-
-__global__ void batch_init_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t k,
-                                  unsigned long long divisor, uint64_t m) {
-    const uint32_t b = threadIdx.x;
-    if (b < kLanes) {
-        ctl->count[b] = b < k ? 1u + (ctr->msgs[b] > 0 ? 1u : 0u) : 0u;
-        ctr->msgs[b] = 0;
-    }
-    __syncwarp();
-    if (b == 0) {
-        ctl->cur = 0;
-        ctl->f = ctr->next_size;
-        ctl->iter = 0;
-        ctl->done = ctr->next_size == 0;
-        ctl->status = 0;
-        ctl->divisor = divisor;
-        ctl->push = batch_push_pick(ctr->edges, divisor, m);
-        ctr->next_size = 0;
-        ctr->status = 0;
-        ctr->edges = 0;
-        ctr->ntasks = 0;
-    }
-}
-
-// End of a superstep: per-source counts, the next frontier becomes current, the
-// counters are cleared for the next superstep, and the WHILE condition says
-// whether the graph runs another one (not past kLoopCap in one launch).
+// End of a superstep: a live lane whose next senders send nothing has finished
+// (its count is final); otherwise it runs another superstep.  The next frontier
+// becomes current, the counters are cleared, and the WHILE condition says
+// whether the graph runs another superstep: while a lane holds a query or the
+// source list has more, not past kLoopCap in one launch, and with host seeding
+// not past a superstep in which a lane finished (or when queries wait for a
+// free lane).
 __global__ void batch_step_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t n,
-                                  uint64_t m, cudaGraphConditionalHandle loop) {
+                                  cudaGraphConditionalHandle loop) {
     const uint32_t b = threadIdx.x;
-    if (b < kLanes) {
-        if (ctr->msgs[b] > 0) ++ctl->count[b];
-        ctr->msgs[b] = 0;
+    const uint32_t live = ctl->live;
+    bool fin = false;
+    if ((live >> b) & 1u) {
+        if (ctr->msgs[b] > 0)
+            ++ctl->count[b];
+        else
+            fin = true;
     }
-    __syncwarp();
+    ctr->msgs[b] = 0;
+    const unsigned finm = __ballot_sync(0xFFFFFFFFu, fin);
+    if (fin && ctl->steps_out) ctl->steps_out[ctl->row[b]] = ctl->count[b];
     if (b == 0) {
         const uint32_t fn = ctr->next_size;
         uint32_t status = ctl->status | ctr->status;
@@ -442,32 +505,45 @@ __global__ void batch_step_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __r
         ctl->status = status;
         ctl->f = fn <= n ? fn : 0u;
         ctl->cur ^= 1u;
-        ctl->push = batch_push_pick(ctr->edges, ctl->divisor, m);
+        ctl->f_edges = ctr->edges;
+        const uint32_t now_live = live & ~finm;
+        ctl->live = now_live;
+        ctl->finished = finm;
         ctr->next_size = 0;
         ctr->status = 0;
         ctr->edges = 0;
         ctr->ntasks = 0;
-        const bool more = ctl->f > 0 && status == 0;
+        const bool from_list = ctl->nqueries != 0;
+        const bool more = (now_live != 0 || (from_list && ctl->next_query < ctl->nqueries)) && status == 0;
+        bool stop = false;
+        if (!from_list && ctl->stop_on_finish) {
+            stop = finm != 0;
+            if (ctl->admit && *ctl->admit && now_live != 0xFFFFFFFFu) stop = true;
+        }
         ctl->done = !more;
         const unsigned it = ctl->iter + 1;
-        const bool again = more && it < kLoopCap;
+        const bool again = more && !stop && it < kLoopCap;
         ctl->iter = again ? it : 0u;
         cudaGraphSetConditional(loop, again ? 1u : 0u);
     }
 }
 
-// out[b][v] = dist[inv[v]][b] for b < k, through a shared-memory transpose
-__global__ void batch_output_kernel(const uint32_t* __restrict__ dist, const uint32_t* __restrict__ inv, uint32_t n,
-                                    uint32_t k, uint32_t* __restrict__ out, uint64_t out_stride) {
-    __shared__ uint32_t tile[32][33];
-    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // 32 warps
-    for (uint64_t v0 = (uint64_t)blockIdx.x * 32; v0 < n; v0 += (uint64_t)gridDim.x * 32) {
-        const uint64_t v = v0 + w;
-        tile[w][lane] = v < n ? dist[(uint64_t)inv[v] * kLanes + lane] : kInf;
-        __syncthreads();
-        const uint64_t vv = v0 + lane;
-        if (w < k && vv < n) out[(uint64_t)w * out_stride + vv] = tile[lane][w];
-        __syncthreads();
+// Finished lanes: out[row][v] = dist[inv[v]][lane] for every caller id v, and the
+// lane's column back to kInf for its next query.
+__global__ void batch_harvest_kernel(const BatchCtl* __restrict__ ctl, const uint32_t* __restrict__ inv, uint32_t n,
+                                     uint32_t* __restrict__ dist) {
+    const uint32_t fin = ctl->finished;
+    if (!fin) return;
+    uint32_t* __restrict__ out = ctl->out;
+    const uint64_t stride = ctl->out_stride;
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += step) {
+        uint32_t* d = dist + (uint64_t)inv[v] * kLanes;
+        for (uint32_t r = fin; r; r &= r - 1) {
+            const uint32_t b = __ffs(r) - 1;
+            out[(uint64_t)ctl->row[b] * stride + v] = d[b];
+            d[b] = kInf;
+        }
     }
 }
 
@@ -489,11 +565,16 @@ struct BatchWorkspace {
     uint32_t* fr[2] = {nullptr, nullptr};
     uint32_t* chunk_row = nullptr;
     uint64_t chunks = 0;
-    uint32_t* src_int = nullptr;  // [32]
     BatchCounters* ctr = nullptr;
     BatchCtl* ctl = nullptr;
-    BatchCtl* h_ctl = nullptr;  // pinned mirror
+    BatchCtl* h_ctl = nullptr;            // pinned mirror
+    unsigned int* h_admit = nullptr;      // mapped host flag (serving)
+    unsigned int* d_admit = nullptr;      // its device address
+    uint32_t* list = nullptr;             // source list (caller ids) of ipg_sssp_batch
+    uint32_t* steps = nullptr;            // per-query superstep counts of ipg_sssp_batch
+    size_t list_cap = 0;
     unsigned long long* tasks = nullptr;  // push tasks of the current senders
+    bool clean = false;                   // dist/sval all kInf, masks and counters zero
     cudaGraphExec_t loop[3] = {nullptr, nullptr, nullptr};  // superstep loop, per weight kind
 };
 
@@ -507,11 +588,13 @@ void batch_free(ipg_graph* g) {
     cudaFree(b->fr[0]);
     cudaFree(b->fr[1]);
     cudaFree(b->chunk_row);
-    cudaFree(b->src_int);
     cudaFree(b->ctr);
     cudaFree(b->ctl);
     cudaFree(b->tasks);
+    cudaFree(b->list);
+    cudaFree(b->steps);
     if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    if (b->h_admit) cudaFreeHost(b->h_admit);
     for (int i = 0; i < 3; ++i)
         if (b->loop[i]) cudaGraphExecDestroy(b->loop[i]);
     delete b;
@@ -530,13 +613,15 @@ static ipg_status batch_prepare(ipg_graph* g, cudaStream_t st) {
     IPG_CUDA(cudaMalloc(&b->cmask, sizeof(uint32_t) * (size_t)n));
     IPG_CUDA(cudaMalloc(&b->fr[0], sizeof(uint32_t) * (size_t)n));
     IPG_CUDA(cudaMalloc(&b->fr[1], sizeof(uint32_t) * (size_t)n));
-    IPG_CUDA(cudaMalloc(&b->src_int, sizeof(uint32_t) * kLanes));
     IPG_CUDA(cudaMalloc(&b->ctr, sizeof(BatchCounters)));
     IPG_CUDA(cudaMalloc(&b->ctl, sizeof(BatchCtl)));
     // a sender with d out-edges makes ceil(d / kPushChunk) <= d / kPushChunk + 1 tasks
     const size_t max_tasks = (size_t)n + g->m / kPushChunk + 1;
     IPG_CUDA(cudaMalloc(&b->tasks, sizeof(unsigned long long) * max_tasks));
     IPG_CUDA(cudaHostAlloc(&b->h_ctl, sizeof(BatchCtl), cudaHostAllocDefault));
+    IPG_CUDA(cudaHostAlloc(&b->h_admit, sizeof(unsigned int), cudaHostAllocMapped));
+    *b->h_admit = 0;
+    IPG_CUDA(cudaHostGetDevicePointer((void**)&b->d_admit, b->h_admit, 0));
     b->chunks = (g->m + kChunk - 1) / kChunk;
     IPG_CUDA(cudaMalloc(&b->chunk_row, sizeof(uint32_t) * (b->chunks ? b->chunks : 1)));
     if (b->chunks) {
@@ -560,6 +645,8 @@ static void batch_superstep(ipg_graph* g, BatchWorkspace* b, int wkind, cudaGrap
 #define IPG_BATCH_PUSH(K)                                                                                         \
     batch_push_kernel<K><<<fixed, 256, 0, st>>>(g->off, g->col, g->w8, g->w, b->tasks, b->sval, b->smask, b->dist,  \
                                                 b->cmask, b->fr[0], b->fr[1], b->ctl, b->ctr)
+    batch_refill_kernel<<<1, kLanes, 0, st>>>(b->ctl, g->inv, g->off, g->m, b->dist, b->sval, b->smask, b->fr[0],
+                                              b->fr[1]);
     batch_tasks_kernel<<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, g->off, b->tasks, b->ctr);
     if (wkind == 1) {
         IPG_BATCH_PULL(1);
@@ -576,7 +663,8 @@ static void batch_superstep(ipg_graph* g, BatchWorkspace* b, int wkind, cudaGrap
     batch_reset_kernel<<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, b->sval, b->smask);
     batch_apply_kernel<<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, g->n, g->off, b->dist, b->sval, b->smask,
                                               b->cmask, b->ctr);
-    batch_step_kernel<<<1, kLanes, 0, st>>>(b->ctl, b->ctr, g->n, g->m, loop);
+    batch_step_kernel<<<1, kLanes, 0, st>>>(b->ctl, b->ctr, g->n, loop);
+    batch_harvest_kernel<<<fixed, 256, 0, st>>>(b->ctl, g->inv, g->n, b->dist);
 }
 
 // Builds the graph [WHILE (cond) { superstep }] for this workspace and weight kind.
@@ -615,46 +703,40 @@ static ipg_status batch_loop_graph(ipg_graph* g, BatchWorkspace* b, int wkind) {
     return rc;
 }
 
-// one group of k <= 32 sources (caller ids) -> out rows [0, k), row stride out_stride
-static ipg_status batch_group(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* out, uint64_t out_stride,
-                              uint32_t* supersteps, cudaStream_t st) {
-    BatchWorkspace* b = (BatchWorkspace*)g->batch;
-    const uint32_t n = g->n;
-    const int sms = sm_count_of(g->device);
-    const int wkind = g->csc_w8 ? 1 : g->csc_w ? 2 : 0;
-    IPG_TRY(batch_loop_graph(g, b, wkind));
-    // caller ids -> internal ids (inv is device-resident)
-    uint32_t h_src[kLanes];
-    for (uint32_t i = 0; i < k; ++i) h_src[i] = sources[i];
-    IPG_CUDA(cudaMemcpyAsync(b->src_int, h_src, sizeof(uint32_t) * k, cudaMemcpyHostToDevice, st));
-    IPG_CUDA(cudaMemsetAsync(b->dist, 0xFF, sizeof(uint32_t) * kLanes * (size_t)n, st));
-    IPG_CUDA(cudaMemsetAsync(b->sval, 0xFF, sizeof(uint32_t) * kLanes * (size_t)n, st));
-    IPG_CUDA(cudaMemsetAsync(b->ctr, 0, sizeof(BatchCounters), st));
-    IPG_CUDA(cudaMemsetAsync(b->smask, 0, sizeof(uint32_t) * (size_t)n, st));
-    IPG_CUDA(cudaMemsetAsync(b->cmask, 0, sizeof(uint32_t) * (size_t)n, st));
-    IPG_TRY(map_to_internal(g, b->src_int, k, st));
-    batch_seed_kernel<<<1, kLanes, 0, st>>>(b->src_int, k, g->off, b->dist, b->sval, b->smask, b->fr[0], b->ctr);
-    IPG_CUDA(cudaGetLastError());
-    batch_init_kernel<<<1, kLanes, 0, st>>>(b->ctl, b->ctr, k, (unsigned long long)batch_divisor_for(g), g->m);
-    IPG_CUDA(cudaGetLastError());
+static int weight_kind(const ipg_graph* g) { return g->csc_w8 ? 1 : g->csc_w ? 2 : 0; }
+
+// Every lane free, values kInf, masks and counters zero (skipped when the last
+// session left them so), and the control block set for a new session.
+static ipg_status batch_session_begin(ipg_graph* g, BatchWorkspace* b, const BatchCtl& init, cudaStream_t st) {
+    const size_t n = g->n;
+    IPG_TRY(batch_loop_graph(g, b, weight_kind(g)));
+    if (!b->clean) {
+        IPG_CUDA(cudaMemsetAsync(b->dist, 0xFF, sizeof(uint32_t) * kLanes * n, st));
+        IPG_CUDA(cudaMemsetAsync(b->sval, 0xFF, sizeof(uint32_t) * kLanes * n, st));
+        IPG_CUDA(cudaMemsetAsync(b->smask, 0, sizeof(uint32_t) * n, st));
+        IPG_CUDA(cudaMemsetAsync(b->cmask, 0, sizeof(uint32_t) * n, st));
+        IPG_CUDA(cudaMemsetAsync(b->ctr, 0, sizeof(BatchCounters), st));
+    }
+    b->clean = false;
+    *b->h_ctl = init;
+    IPG_CUDA(cudaMemcpyAsync(b->ctl, b->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, st));
+    return IPG_OK;
+}
+
+static BatchCtl batch_ctl_init(const ipg_graph* g) {
+    BatchCtl c;
+    memset(&c, 0, sizeof(c));
+    c.divisor = (unsigned long long)batch_divisor_for(g);
+    return c;
+}
+
+// one graph launch, then the control block back on the host
+static ipg_status batch_launch(ipg_graph* g, BatchWorkspace* b, cudaStream_t st, const char* name) {
+    IPG_CUDA(cudaGraphLaunch(b->loop[weight_kind(g)], st));
     IPG_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
     IPG_CUDA(cudaStreamSynchronize(st));
-    // each launch runs supersteps on the device until the frontier is empty or kLoopCap
-    for (uint64_t launches = 0; !b->h_ctl->done; ++launches) {
-        if (launches > (uint64_t)n / kLoopCap + 2)
-            return set_error(IPG_EDEVICE, "ipg_sssp_batch: the superstep loop did not end after n supersteps");
-        IPG_CUDA(cudaGraphLaunch(b->loop[wkind], st));
-        IPG_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
-        IPG_CUDA(cudaStreamSynchronize(st));
-        if (b->h_ctl->status & kStatusOverflow)
-            return set_error(IPG_EOVERFLOW, "ipg_sssp_batch: a path length reached UINT32_MAX");
-        if (b->h_ctl->status & kStatusInternal) return set_error(IPG_EDEVICE, "ipg_sssp_batch: frontier overflow");
-    }
-    batch_output_kernel<<<grid_for_warps((uint64_t)n, sms), 1024, 0, st>>>(b->dist, g->inv, n, k, out, out_stride);
-    IPG_CUDA(cudaGetLastError());
-    IPG_CUDA(cudaStreamSynchronize(st));
-    if (supersteps)
-        for (uint32_t i = 0; i < k; ++i) supersteps[i] = b->h_ctl->count[i];
+    if (b->h_ctl->status & kStatusOverflow) return set_error(IPG_EOVERFLOW, "%s: a path length reached UINT32_MAX", name);
+    if (b->h_ctl->status & kStatusInternal) return set_error(IPG_EDEVICE, "%s: frontier overflow", name);
     return IPG_OK;
 }
 
@@ -669,12 +751,97 @@ ipg_status sssp_batch_run(ipg_graph* g, const uint32_t* sources, uint32_t k, uin
     DeviceGuard guard(g->device);
     if (!guard.ok) return set_error(IPG_ECUDA, "ipg_sssp_batch: cannot select the graph's device");
     IPG_TRY(batch_prepare(g, st));
-    for (uint32_t i0 = 0; i0 < k; i0 += kLanes) {
-        const uint32_t kk = k - i0 < (uint32_t)kLanes ? k - i0 : (uint32_t)kLanes;
-        IPG_TRY(batch_group(g, sources + i0, kk, dist_dev + (uint64_t)i0 * g->n, g->n,
-                            supersteps_out ? supersteps_out + i0 : nullptr, st));
+    BatchWorkspace* b = (BatchWorkspace*)g->batch;
+    if (b->list_cap < k) {
+        cudaFree(b->list);
+        cudaFree(b->steps);
+        b->list = b->steps = nullptr;
+        b->list_cap = 0;
+        IPG_CUDA(cudaMalloc(&b->list, sizeof(uint32_t) * k));
+        IPG_CUDA(cudaMalloc(&b->steps, sizeof(uint32_t) * k));
+        b->list_cap = k;
+    }
+    IPG_CUDA(cudaMemcpyAsync(b->list, sources, sizeof(uint32_t) * k, cudaMemcpyHostToDevice, st));
+    BatchCtl init = batch_ctl_init(g);
+    init.nqueries = k;
+    init.src_list = b->list;
+    init.steps_out = b->steps;
+    init.out = dist_dev;
+    init.out_stride = g->n;
+    IPG_TRY(batch_session_begin(g, b, init, st));
+    // every lane is refilled on the device: one launch per kLoopCap supersteps
+    const uint64_t bound = ((uint64_t)k + kLanes) * ((uint64_t)g->n + 2) / kLoopCap + 2;
+    for (uint64_t launches = 0;; ++launches) {
+        if (launches > bound)
+            return set_error(IPG_EDEVICE, "ipg_sssp_batch: the superstep loop did not end");
+        IPG_TRY(batch_launch(g, b, st, "ipg_sssp_batch"));
+        if (b->h_ctl->done) break;
+    }
+    b->clean = true;  // every lane was harvested
+    if (supersteps_out) {
+        IPG_CUDA(cudaMemcpyAsync(supersteps_out, b->steps, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost, st));
+        IPG_CUDA(cudaStreamSynchronize(st));
     }
     return IPG_OK;
+}
+
+// ---- lane sessions driven by the host (the server) ------------------------------
+
+ipg_status lanes_open(ipg_graph* g, uint32_t* stage_dev, cudaStream_t st) {
+    DeviceGuard guard(g->device);
+    IPG_TRY(batch_prepare(g, st));
+    BatchWorkspace* b = (BatchWorkspace*)g->batch;
+    *b->h_admit = 0;
+    BatchCtl init = batch_ctl_init(g);
+    init.stop_on_finish = 1;
+    init.admit = b->d_admit;
+    init.out = stage_dev;
+    init.out_stride = g->n;
+    return batch_session_begin(g, b, init, st);
+}
+
+volatile unsigned int* lanes_admit_flag(ipg_graph* g) {
+    BatchWorkspace* b = (BatchWorkspace*)g->batch;
+    return b ? b->h_admit : nullptr;
+}
+
+ipg_status lanes_step(ipg_graph* g, const uint32_t* sources, const uint32_t* rows, uint32_t nseed,
+                      cudaStream_t st, LaneReport* rep) {
+    DeviceGuard guard(g->device);
+    BatchWorkspace* b = (BatchWorkspace*)g->batch;
+    if (!b) return set_error(IPG_EINVAL, "lanes_step: no open session");
+    BatchCtl* h = b->h_ctl;  // mirrors the device block after the previous launch
+    if (nseed > (uint32_t)__builtin_popcount(~h->live)) return set_error(IPG_EINVAL, "lanes_step: too many seeds");
+    if (nseed) {
+        h->nseed = nseed;
+        for (uint32_t i = 0; i < nseed; ++i) {
+            if (sources[i] >= g->n) return set_error(IPG_EINVAL, "lanes_step: source %u >= n", sources[i]);
+            h->seed_src[i] = sources[i];
+            h->seed_row[i] = rows[i];
+        }
+        const size_t beg = offsetof(BatchCtl, nseed), end = offsetof(BatchCtl, out);
+        IPG_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(b->ctl) + beg, reinterpret_cast<char*>(h) + beg, end - beg,
+                                 cudaMemcpyHostToDevice, st));
+    }
+    if (!nseed && h->live == 0) {
+        rep->live = 0;
+        rep->finished = 0;
+        return IPG_OK;
+    }
+    *b->h_admit = 0;
+    IPG_TRY(batch_launch(g, b, st, "lanes_step"));
+    rep->live = h->live;
+    rep->finished = h->finished;
+    for (int l = 0; l < kLanes; ++l) {
+        rep->row[l] = h->row[l];
+        rep->count[l] = h->count[l];
+    }
+    return IPG_OK;
+}
+
+void lanes_close(ipg_graph* g) {
+    BatchWorkspace* b = (BatchWorkspace*)g->batch;
+    if (b && b->h_ctl->live == 0 && b->h_ctl->status == 0) b->clean = true;
 }
 
 }  // namespace ipg

@@ -2,6 +2,7 @@
 // pull-based supersteps, error reporting and small shared helpers.
 #include <stdarg.h>
 #include <atomic>
+#include <chrono>
 #include <stdio.h>
 #include <string.h>
 
@@ -589,6 +590,7 @@ void release_workspace(ipg_graph* g) {
     f(g->val_stage);
     f(g->val);
     f(g->sval);
+    f(g->sbits);
     batch_free(g);
     generic_free(g);
 }
@@ -613,6 +615,7 @@ static void free_graph(ipg_graph* g) {
     f(g->inv);
     f(g->val);
     f(g->sval);
+    f(g->sbits);
     f(g->pr_rank);
     f(g->inv_outdeg);
     f(g->pr_box[0]);
@@ -660,6 +663,10 @@ static ipg_status create_impl(const uint64_t* offsets, const uint32_t* columns, 
     ipg_graph* g = new (std::nothrow) ipg_graph();
     if (!g) return set_error(IPG_ENOMEM, "ipg_graph_create: host allocation failed");
     ipg_status rc = IPG_OK;
+    using clk = std::chrono::steady_clock;
+    const auto t_begin = clk::now();
+    auto ms_since = [](clk::time_point a) { return std::chrono::duration<float, std::milli>(clk::now() - a).count(); };
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     do {
         if (cudaGetDevice(&g->device) != cudaSuccess) {
             rc = set_error(IPG_ECUDA, "ipg_graph_create: no CUDA device");
@@ -681,12 +688,18 @@ static ipg_status create_impl(const uint64_t* offsets, const uint32_t* columns, 
         CR(cudaMalloc(&g->off, sizeof(uint64_t) * ((size_t)n + 1)));
         CR(cudaMalloc(&g->col, sizeof(uint32_t) * (m ? m : 1)));
         if (weights) CR(cudaMalloc(&g->w, sizeof(uint32_t) * (m ? m : 1)));
+        for (auto& x : ev) CR(cudaEventCreate(&x));
+        g->create_profile.alloc_ms = ms_since(t_begin);
         cudaStream_t st = from_device ? user_stream : g->stream;
         cudaMemcpyKind kind = from_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         CR(cudaMemsetAsync(g->counters, 0, sizeof(PushCounters), st));
+        const auto t_copy = clk::now();
+        CR(cudaEventRecord(ev[0], st));
         CR(cudaMemcpyAsync(g->off, offsets, sizeof(uint64_t) * ((size_t)n + 1), kind, st));
         if (m) CR(cudaMemcpyAsync(g->col, columns, sizeof(uint32_t) * m, kind, st));
         if (weights && m) CR(cudaMemcpyAsync(g->w, weights, sizeof(uint32_t) * m, kind, st));
+        CR(cudaEventRecord(ev[1], st));
+        g->create_profile.upload_issue_ms = ms_since(t_copy);
         int sms = device_sms(g->device);
         validate_offsets_kernel<<<grid_for((uint64_t)n + 1, sms), 256, 0, st>>>(g->off, n, m, &g->counters->status);
         CR(cudaGetLastError());
@@ -694,8 +707,11 @@ static ipg_status create_impl(const uint64_t* offsets, const uint32_t* columns, 
             validate_columns_kernel<<<grid_for(m, sms, 16), 256, 0, st>>>(g->col, m, n, &g->counters->status);
             CR(cudaGetLastError());
         }
+        CR(cudaEventRecord(ev[2], st));
         CR(cudaMemcpyAsync(g->h_counters, g->counters, sizeof(PushCounters), cudaMemcpyDeviceToHost, st));
         CR(cudaStreamSynchronize(st));
+        CR(cudaEventElapsedTime(&g->create_profile.upload_ms, ev[0], ev[1]));
+        CR(cudaEventElapsedTime(&g->create_profile.validate_ms, ev[1], ev[2]));
 #undef CR
         unsigned status = g->h_counters->status;
         if (status & kStatusBadCsr) {
@@ -707,8 +723,11 @@ static ipg_status create_impl(const uint64_t* offsets, const uint32_t* columns, 
             rc = set_error(IPG_EINVAL, "ipg_graph_create: a column index is >= n");
             break;
         }
+        const auto t_relabel = clk::now();
         rc = relabel(g, st);
         if (rc != IPG_OK) break;
+        g->create_profile.renumber_ms = ms_since(t_relabel);
+        g->create_profile.total_ms = ms_since(t_begin);
         if (!g->directed) {
             g->csc_off = g->off;
             g->csc_src = g->col;
@@ -717,6 +736,8 @@ static ipg_status create_impl(const uint64_t* offsets, const uint32_t* columns, 
             g->csc_ready = true;
         }
     } while (0);
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
     if (rc != IPG_OK) {
         free_graph(g);
         return rc;
@@ -976,6 +997,12 @@ ipg_status ipg_graph_create_dev(const uint64_t* offsets_dev, const uint32_t* col
 
 void ipg_graph_destroy(ipg_graph* g) { free_graph(g); }
 
+ipg_status ipg_graph_create_profile(const ipg_graph* g, ipg_create_profile* out) {
+    if (!g || !out) return set_error(IPG_EINVAL, "ipg_graph_create_profile: NULL argument");
+    *out = g->create_profile;
+    return IPG_OK;
+}
+
 ipg_status ipg_graph_info(const ipg_graph* g, uint32_t* n, uint64_t* m, int* directed, int* weighted) {
     if (!g) return set_error(IPG_EINVAL, "ipg_graph_info: graph is NULL");
     if (n) *n = g->n;
@@ -1049,6 +1076,11 @@ ipg_status ipg_set_tuning(const char* name, int64_t value) {
         tuning().pr_carveout = value;
         return IPG_OK;
     }
+    if (!strcmp(name, "pull_filter")) {
+        if (value < 0 || value > 100) return set_error(IPG_EINVAL, "ipg_set_tuning: pull_filter must be in [0, 100]");
+        tuning().pull_filter = value;
+        return IPG_OK;
+    }
     return set_error(IPG_EINVAL, "ipg_set_tuning: unknown knob '%s'", name);
 }
 
@@ -1080,6 +1112,10 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value) {
     }
     if (!strcmp(name, "pr_carveout")) {
         *value = tuning().pr_carveout;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "pull_filter")) {
+        *value = tuning().pull_filter;
         return IPG_OK;
     }
     return set_error(IPG_EINVAL, "ipg_get_tuning: unknown knob '%s'", name);

@@ -39,9 +39,11 @@ struct PushLoop {
     unsigned int count;    // superstep count once done
     unsigned int nrec;     // stats records written
     unsigned int status;   // kStatus* bits
-    unsigned int pad;
+    unsigned int filter;   // 1: this pull superstep checks the sender bits before each gather
     unsigned long long divisor;         // pull when messages * divisor >= m (0: never)
     unsigned long long prev_receivers;  // receivers of the previous superstep (stats mode)
+    unsigned int filter_pct;            // filter a pull superstep whose messages are below this % of m
+    unsigned int pad;
 };
 
 // frontier of a loop-driven superstep (loop != NULL) or of a host-driven one
@@ -162,6 +164,8 @@ struct ipg_graph {
     uint32_t* val = nullptr;                  // values in internal numbering
     float* pr_rank = nullptr;                 // final ranks in internal numbering
     uint32_t* sval = nullptr;                 // pull supersteps: value sent by each vertex, kInf if none
+    uint32_t* sbits = nullptr;                // pull supersteps: one bit per vertex, set for the senders
+    ipg_create_profile create_profile{};      // where ipg_graph_create spent its time
     ipg::PushCounters* counters = nullptr;    // device
     ipg::PushCounters* h_counters = nullptr;  // pinned host mirror
 
@@ -206,6 +210,23 @@ ipg_status frontier_prepare(ipg_graph* g, const uint32_t* F, uint32_t f, const u
 ipg_status frontier_partition(ipg_graph* g, uint32_t f, cudaStream_t st);
 // in ipg_batch.cu
 void batch_free(ipg_graph* g);
+// Lane sessions of the batched SSSP engine driven by the host (the server): up to
+// 32 queries run at once, one per lane; seeds join at superstep boundaries.
+struct LaneReport {
+    uint32_t live;          // lanes holding a query after the launch
+    uint32_t finished;      // lanes whose query finished in the launch's last superstep
+    uint32_t row[32];       // output (staging) row of each lane's query
+    uint32_t count[32];     // superstep count of each lane's query (final for finished lanes)
+};
+// stage_dev: 32 rows of n words; a finished query's distances land in its row.
+ipg_status lanes_open(ipg_graph* g, uint32_t* stage_dev, cudaStream_t st);
+// Seeds nseed queries (caller-id sources, staging rows; at most the free lanes),
+// then runs supersteps until a lane finishes or the admit flag is raised.
+ipg_status lanes_step(ipg_graph* g, const uint32_t* sources, const uint32_t* rows, uint32_t nseed,
+                      cudaStream_t st, LaneReport* rep);
+void lanes_close(ipg_graph* g);
+// mapped host flag that ends a running launch at the next superstep boundary
+volatile unsigned int* lanes_admit_flag(ipg_graph* g);
 ipg_status sssp_batch_run(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_dev,
                           uint32_t* supersteps_out, cudaStream_t st);
 // in ipg_generic.cu
@@ -213,7 +234,7 @@ void generic_free(ipg_graph* g);
 // caller ids -> internal ids, in place on the device
 ipg_status map_to_internal(ipg_graph* g, uint32_t* ids, uint32_t k, cudaStream_t st);
 // in ipg_pull_min.cu
-ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, const uint32_t* F, const uint32_t* fval, uint32_t f,
+ipg_status pull_min_superstep(ipg_graph* g, bool sssp, bool recv, bool filter, const uint32_t* F, const uint32_t* fval, uint32_t f,
                               uint32_t* val, uint32_t* next, cudaStream_t st, cudaEvent_t ev_kernel);
 // the pull form of a loop-driven superstep: every kernel returns at once unless
 // loop->pull is set; frontiers and sizes come from the loop block
@@ -228,6 +249,7 @@ struct Tuning {
     long long batch_divisor = 6; // batched SSSP: push when the senders' out-edges < m / batch_divisor (0 = pull)
     long long push_loop = 1;     // Hashmin/SSSP: 1 = superstep loop in a CUDA graph where possible, 0 = host loop
     long long pr_engine = 0;     // PageRank pull kernel: 0 staged messages, 1 direct (registers)
+    long long pull_filter = 0;   // Hashmin/SSSP pull: check sender bits first below this % of m messages; 0 = never
 };
 Tuning& tuning();
 // the graph's tuned value where it has one, else the process-wide knob

@@ -158,8 +158,10 @@ __global__ void __launch_bounds__(kScanThreads) fr_scan_kernel(unsigned long lon
         ctr->tiles = (unsigned)(((unsigned long long)f + total + kPushTile - 1) / kPushTile);
         ctr->next_size = 0;
         ctr->receivers = 0;
-        if (loop)
+        if (loop) {
             loop->pull = loop->divisor > 0 && total > 0 && (double)total * (double)loop->divisor >= (double)m;
+            loop->filter = loop->pull && (double)total * 100.0 < (double)m * (double)loop->filter_pct;
+        }
     }
 }
 
@@ -477,7 +479,10 @@ void relax_dispatch(int kind, bool recv, unsigned grid, cudaStream_t st, ipg_gra
 constexpr unsigned kLoopCap = 64;          // supersteps per graph launch
 constexpr uint32_t kLoopRecords = 1 << 16; // stats records a loop-driven run keeps
 
-__global__ void loop_init_kernel(PushLoop* __restrict__ loop, uint32_t f, unsigned long long divisor) {
+__global__ void loop_init_kernel(PushLoop* __restrict__ loop, uint32_t f, unsigned long long divisor,
+                                 unsigned int filter_pct) {
+    loop->filter = 0;
+    loop->filter_pct = filter_pct;
     loop->cur = 0;
     loop->f = f;
     loop->s = 0;
@@ -664,7 +669,8 @@ ipg_status push_run_loop(ipg_graph* g, int kind, uint32_t source, uint32_t* out,
         sssp_init_kernel<<<grid_cap(n), 256, 0, st>>>(g->val, g->frontier[0], n, g->inv, source);
         f = 1;
     }
-    loop_init_kernel<<<1, 1, 0, st>>>(g->loop, f, (unsigned long long)(div > 0 ? div : 0));
+    loop_init_kernel<<<1, 1, 0, st>>>(g->loop, f, (unsigned long long)(div > 0 ? div : 0),
+                                      (unsigned int)tuning().pull_filter);
     IPG_CUDA(cudaGetLastError());
     // each launch runs up to kLoopCap supersteps; a run has at most n + 1
     const uint64_t max_launches = (uint64_t)n / kLoopCap + 3;
@@ -761,7 +767,7 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
                                      cudaMemcpyDeviceToHost, st));
         }
         // direction: a superstep whose messages reach m / pull_divisor runs in pull form
-        bool pull = false;
+        bool pull = false, filter = false;
         const long long div = pull_divisor_for(g, kind == kSssp);
         // a frontier of f vertices sends at most f * max_outdeg messages: read the exact
         // count back (one more host sync) only when that bound reaches m / pull_divisor
@@ -771,9 +777,10 @@ ipg_status push_run(ipg_graph* g, int kind, uint32_t source, uint32_t* out, ipg_
             IPG_CUDA(cudaStreamSynchronize(st));
             const unsigned long long es = g->h_counters->edges;
             pull = es > 0 && (double)es * (double)div >= (double)g->m;
+            filter = pull && (double)es * 100.0 < (double)g->m * (double)tuning().pull_filter;
         }
         if (pull) {
-            IPG_TRY(pull_min_superstep(g, kind == kSssp, recv, g->frontier[cur], g->fr_val, f, val,
+            IPG_TRY(pull_min_superstep(g, kind == kSssp, recv, filter, g->frontier[cur], g->fr_val, f, val,
                                        g->frontier[cur ^ 1], st, timing ? ev[1] : nullptr));
         } else {
             IPG_TRY(frontier_partition(g, f, st));

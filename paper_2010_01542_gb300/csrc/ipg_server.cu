@@ -4,11 +4,18 @@
 // Every graph has a FIFO of pending queries.  Worker threads take the oldest
 // waiting graph that no other worker is running (calls on one graph share its
 // workspace and must not overlap) and dispatch:
-//   - all of that graph's queued SSSP queries together, up to max_batch, through
-//     the batched SSSP engine (queries that arrived while the previous dispatch
-//     was on the GPU join the next one: continuous batching); below
-//     min_sssp_batch queries (16 by default) the dispatch runs them one source
-//     at a time, which is faster there;
+//   - SSSP queries at the head of the graph's queue: with at least
+//     min_sssp_batch of them queued (16 by default) a lane session of the
+//     batched engine starts: each query takes one of 32 lanes, and whenever a
+//     lane's query finishes (its run quiesced) the lane is harvested and the next
+//     SSSP query at the head of the queue takes it at the following superstep
+//     boundary, so queries that arrive while others are on the GPU join the
+//     running batch (continuous batching).  A submit for a graph in a session
+//     raises a flag in mapped host memory that ends the running graph launch at
+//     the next superstep boundary when a lane is free.  The session admits no
+//     query from behind a queued Hashmin or PageRank query (first come, first
+//     served per graph), and ends when its lanes are empty.  With fewer SSSP
+//     queries queued they run one source at a time, which is faster there;
 //   - otherwise the head query's kind (Hashmin, or PageRank with the same update
 //     count): every such query queued on the graph shares one run, since they
 //     compute the same result (in flight only: finished results are not reused).
@@ -40,6 +47,7 @@ struct ipg_server {
         ipg_graph* g = nullptr;
         std::deque<Pending> pending;
         bool busy = false;
+        bool session = false;  // a worker runs an SSSP lane session on this graph
         uint64_t last_used = 0;
         size_t held = 0;  // workspace bytes this graph holds (estimate)
     };
@@ -154,6 +162,116 @@ struct WorkerBuffers {
     }
 };
 
+// An SSSP lane session on slot `pick` (the caller holds the lock and has marked
+// the slot busy; `first` are the head queries to seed, at most 32).  Returns with
+// the lock held.
+void run_session(ipg_server* s, std::unique_lock<std::mutex>& lock, int pick, std::vector<ipg_server::Pending> first,
+                 WorkerBuffers& buf) {
+    auto& slot = s->slots[pick];
+    ipg_graph* g = slot.g;
+    const size_t n = g->n;
+    const uint32_t cap = std::min<uint32_t>(32, std::max<uint32_t>(1, s->max_batch));
+    slot.session = true;
+    lock.unlock();
+    struct LiveQuery {
+        ipg_server::Pending p;
+        double t_start = 0;
+        uint32_t batch = 0;
+        uint32_t joined = 0;
+    };
+    std::vector<LiveQuery> by_row(32);
+    std::vector<uint32_t> free_rows;
+    for (int r = 31; r >= 0; --r) free_rows.push_back((uint32_t)r);
+    uint32_t live_count = 0;
+    ipg_status rc = buf.reserve(32 * n);
+    if (rc == IPG_OK) rc = lanes_open(g, buf.dev, g->stream);
+    std::vector<ipg_server::Pending> seeds = std::move(first);
+    bool opened = true;
+    std::vector<ipg_completion> out;
+    for (;;) {
+        uint32_t src[32], rows[32];
+        const double t_seed = s->now();
+        for (size_t i = 0; i < seeds.size(); ++i) {
+            const uint32_t r = free_rows.back();
+            free_rows.pop_back();
+            by_row[r].p = seeds[i];
+            by_row[r].t_start = t_seed;
+            by_row[r].batch = live_count + (uint32_t)seeds.size();
+            by_row[r].joined = opened ? 0u : 1u;
+            src[i] = seeds[i].q.source;
+            rows[i] = r;
+        }
+        live_count += (uint32_t)seeds.size();
+        LaneReport rep{};
+        if (rc == IPG_OK) rc = lanes_step(g, src, rows, (uint32_t)seeds.size(), g->stream, &rep);
+        seeds.clear();
+        opened = false;
+        out.clear();
+        if (rc != IPG_OK) {
+            // every query of the session fails with the same status
+            for (uint32_t r = 0; r < 32; ++r) {
+                if (std::find(free_rows.begin(), free_rows.end(), r) != free_rows.end()) continue;
+                ipg_completion c{};
+                c.user = by_row[r].p.q.user;
+                c.status = rc;
+                c.batch = by_row[r].batch;
+                c.joined = by_row[r].joined;
+                c.t_submit = by_row[r].p.t_submit;
+                c.t_start = by_row[r].t_start;
+                c.t_done = s->now();
+                out.push_back(c);
+                free_rows.push_back(r);
+            }
+            live_count = 0;
+        } else {
+            for (uint32_t fin = rep.finished; fin; fin &= fin - 1) {
+                const int l = __builtin_ctz(fin);
+                const uint32_t r = rep.row[l];
+                cudaError_t e = cudaMemcpyAsync(by_row[r].p.q.out, buf.dev + (size_t)r * n, sizeof(uint32_t) * n,
+                                                cudaMemcpyDeviceToHost, g->stream);
+                ipg_completion c{};
+                c.user = by_row[r].p.q.user;
+                c.status = e == cudaSuccess ? IPG_OK : cuda_fail(e, "server result copy", __FILE__, __LINE__);
+                c.supersteps = rep.count[l];
+                c.batch = by_row[r].batch;
+                c.joined = by_row[r].joined;
+                c.t_submit = by_row[r].p.t_submit;
+                c.t_start = by_row[r].t_start;
+                out.push_back(c);
+                free_rows.push_back(r);
+                --live_count;
+            }
+            if (!out.empty()) {
+                cudaError_t e = cudaStreamSynchronize(g->stream);
+                if (e != cudaSuccess) {
+                    const ipg_status bad = cuda_fail(e, "server result copy", __FILE__, __LINE__);
+                    for (auto& c : out) c.status = bad;
+                }
+            }
+        }
+        const double t_done = s->now();
+        lock.lock();
+        for (auto& c : out) {
+            c.t_done = t_done;
+            s->done.push_back(c);
+        }
+        s->inflight -= out.size();
+        if (!out.empty()) s->cv_done.notify_all();
+        // admission at this superstep boundary: SSSP queries at the head of the queue
+        volatile unsigned int* flag = lanes_admit_flag(g);
+        if (flag) *flag = 0;
+        if (rc == IPG_OK)
+            while (!slot.pending.empty() && slot.pending.front().q.kind == IPG_Q_SSSP && live_count + seeds.size() < cap) {
+                seeds.push_back(slot.pending.front());
+                slot.pending.pop_front();
+            }
+        if (live_count == 0 && seeds.empty()) break;
+        lock.unlock();
+    }
+    slot.session = false;
+    lanes_close(g);
+}
+
 void finish(ipg_server* s, const std::vector<ipg_server::Pending>& batch, const std::vector<ipg_status>& rc,
             const std::vector<uint32_t>& steps, double t_start, double t_done) {
     for (size_t i = 0; i < batch.size(); ++i) {
@@ -193,7 +311,16 @@ void worker_main(ipg_server* s) {
         auto& slot = s->slots[pick];
         std::vector<ipg_server::Pending> batch;
         const uint32_t kind = slot.pending.front().q.kind;
-        if (kind == IPG_Q_SSSP) {
+        size_t head_sssp = 0;  // SSSP queries at the head of the queue
+        for (auto it = slot.pending.begin(); it != slot.pending.end() && it->q.kind == IPG_Q_SSSP; ++it) ++head_sssp;
+        const bool session = kind == IPG_Q_SSSP && head_sssp >= s->min_batch && s->max_batch > 1;
+        if (session) {
+            const size_t cap = std::min<size_t>(32, s->max_batch);
+            while (batch.size() < cap && !slot.pending.empty() && slot.pending.front().q.kind == IPG_Q_SSSP) {
+                batch.push_back(slot.pending.front());
+                slot.pending.pop_front();
+            }
+        } else if (kind == IPG_Q_SSSP) {
             for (auto it = slot.pending.begin(); it != slot.pending.end() && batch.size() < s->max_batch;) {
                 if (it->q.kind == IPG_Q_SSSP) {
                     batch.push_back(*it);
@@ -216,7 +343,8 @@ void worker_main(ipg_server* s) {
             }
         }
         // admission by device memory
-        const size_t need = workspace_need(slot.g, kind, (uint32_t)batch.size(), s->min_batch);
+        const size_t need = workspace_need(slot.g, kind, session ? s->min_batch : (uint32_t)batch.size(),
+                                           s->min_batch);
         for (;;) {
             size_t avail;
             if (s->budget) {
@@ -249,40 +377,26 @@ void worker_main(ipg_server* s) {
         slot.last_used = ++s->tick;
         slot.held += need;
         ipg_graph* g = slot.g;
-        const bool batched = kind == IPG_Q_SSSP && batch.size() >= s->min_batch;
+        if (session) {
+            run_session(s, lock, pick, std::move(batch), buf);
+            slot.busy = false;
+            s->cv_done.notify_all();
+            s->cv_work.notify_all();
+            continue;
+        }
         lock.unlock();
 
         const double t_start = s->now();
         std::vector<ipg_status> rc(batch.size(), IPG_OK);
         std::vector<uint32_t> steps(batch.size(), 0);
-        if (kind == IPG_Q_SSSP && !batched) {
-            // a few sources: one-source runs (push for sparse supersteps) beat a batch,
-            // which streams every in-edge once per superstep
+        if (kind == IPG_Q_SSSP) {
+            // a few sources: one-source runs (push for sparse supersteps) beat a lane
+            // session, whose pull supersteps stream every in-edge
             for (size_t i = 0; i < batch.size(); ++i) {
                 ipg_stats st{nullptr, 0, 0, 0, 0};
                 rc[i] = ipg_sssp(g, batch[i].q.source, (uint32_t*)batch[i].q.out, &st);
                 steps[i] = st.count;
             }
-        } else if (kind == IPG_Q_SSSP) {
-            // groups of kStageSources (the engine's group size) through a staging buffer
-            const size_t k = batch.size(), n = g->n;
-            ipg_status r = buf.reserve(kStageSources * n);
-            std::vector<uint32_t> src(k);
-            for (size_t i = 0; i < k; ++i) src[i] = batch[i].q.source;
-            for (size_t i0 = 0; i0 < k && r == IPG_OK; i0 += kStageSources) {
-                const size_t kk = k - i0 < kStageSources ? k - i0 : kStageSources;
-                r = sssp_batch_run(g, src.data() + i0, (uint32_t)kk, buf.dev, steps.data() + i0, g->stream);
-                for (size_t i = 0; i < kk && r == IPG_OK; ++i) {
-                    cudaError_t e = cudaMemcpyAsync(batch[i0 + i].q.out, buf.dev + i * n, sizeof(uint32_t) * n,
-                                                    cudaMemcpyDeviceToHost, g->stream);
-                    if (e != cudaSuccess) r = cuda_fail(e, "server result copy", __FILE__, __LINE__);
-                }
-                if (r == IPG_OK) {
-                    cudaError_t e = cudaStreamSynchronize(g->stream);
-                    if (e != cudaSuccess) r = cuda_fail(e, "server result copy", __FILE__, __LINE__);
-                }
-            }
-            std::fill(rc.begin(), rc.end(), r);
         } else if (kind == IPG_Q_HASHMIN || kind == IPG_Q_PAGERANK) {
             ipg_stats st{nullptr, 0, 0, 0, 0};
             const ipg_status r = kind == IPG_Q_HASHMIN
@@ -370,8 +484,14 @@ ipg_status ipg_server_submit(ipg_server* s, const ipg_query* q) {
     if (g->n && !q->out) return set_error(IPG_EINVAL, "ipg_server_submit: output is NULL");
     {
         std::lock_guard<std::mutex> lock(s->mu);
-        s->slots[q->graph].pending.push_back({*q, s->now()});
+        auto& slot = s->slots[q->graph];
+        slot.pending.push_back({*q, s->now()});
         s->inflight++;
+        if (slot.session && q->kind == IPG_Q_SSSP) {
+            // end the session's running launch at the next superstep boundary
+            volatile unsigned int* flag = lanes_admit_flag(slot.g);
+            if (flag) *flag = 1;
+        }
     }
     s->cv_work.notify_one();
     return IPG_OK;

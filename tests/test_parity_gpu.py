@@ -33,13 +33,18 @@ def ipg():
 ALWAYS_PULL = 1 << 40  # any superstep with a message runs in pull form
 
 
-@pytest.fixture(params=["auto", "push", "pull"])
+@pytest.fixture(params=["auto", "push", "pull", "pull-filtered"])
 def direction(request, ipg, driver):
-    """Runs a Hashmin/SSSP test with the automatic push/pull switch, always push, or always pull."""
+    """Runs a Hashmin/SSSP test with the automatic push/pull switch, always push, always pull
+    with plain gathers, or always pull with the sender bits read before every gather."""
     old = ipg.ipg_get_tuning("pull_divisor")
-    ipg.ipg_set_tuning("pull_divisor", {"auto": old, "push": 0, "pull": ALWAYS_PULL}[request.param])
-    yield request.param
+    old_filter = ipg.ipg_get_tuning("pull_filter")
+    mode = request.param
+    ipg.ipg_set_tuning("pull_divisor", {"auto": old, "push": 0}.get(mode, ALWAYS_PULL))
+    ipg.ipg_set_tuning("pull_filter", {"pull": 0, "pull-filtered": 100}.get(mode, old_filter))
+    yield mode
     ipg.ipg_set_tuning("pull_divisor", old)
+    ipg.ipg_set_tuning("pull_filter", old_filter)
 
 
 @pytest.fixture(params=["graph-loop", "host-loop"])

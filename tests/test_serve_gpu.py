@@ -153,3 +153,39 @@ def test_cancel_queued_queries(ipg):
         if k:
             break
     assert cancelled_total > 0
+
+
+def test_queries_join_a_running_lane_session(ipg):
+    """SSSP queries submitted while a lane session runs on the graph are seeded into free
+    lanes at superstep boundaries (completion.joined == 1); every result equals the oracle's
+    and the query run alone, whichever superstep it joined at."""
+    import time
+
+    import oracle
+
+    g = gen.rmat(15, 16, seed=31, undirected=True, weighted=True)
+    h = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, False)
+    rng = np.random.default_rng(31)
+    sources = [int(x) for x in rng.integers(0, g.n, size=120)]
+    srv = ipg.Server([h], workers=1, min_sssp_batch=4, prepare=True)
+    outs = {}
+    for u, src in enumerate(sources):
+        outs[u] = np.empty(g.n, dtype=np.uint32)
+        srv.submit(0, ipg.IPG_Q_SSSP, outs[u], source=src, user=u)
+        if u >= 8:
+            time.sleep(0.0005)  # later queries arrive while the first ones run
+    srv.drain()
+    done = srv.poll(0)
+    srv.close()
+    assert len(done) == len(sources)
+    joined = 0
+    for c in done:
+        assert c.status == 0
+        ref, cnt, _ = ipg.ipg_sssp(h, sources[c.user])
+        np.testing.assert_array_equal(c.out, ref)
+        assert c.supersteps == cnt
+        joined += c.joined
+    assert joined > 0
+    for u in range(0, len(sources), 15):  # a sample against the oracle
+        o = oracle.sssp(g.n, g.offsets, g.cols, g.weights, sources[u])
+        np.testing.assert_array_equal(outs[u], o.values)

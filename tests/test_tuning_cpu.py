@@ -22,6 +22,7 @@ KNOBS = {
     "pr_carveout": ([-1, 0, 50, 100], [-2, 101]),
     "batch_divisor": ([0, 1, 6, 1 << 40], [-1]),
     "push_loop": ([0, 1], [2, -1]),
+    "pull_filter": ([0, 60, 100], [-1, 101]),
 }
 
 
