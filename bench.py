@@ -672,6 +672,7 @@ def run_batch(a):
     e1.record(stream)
     torch.cuda.synchronize()
     t_batch = all_max(e0.elapsed_time(e1) / a.steps, world)
+    binfo = ipg.ipg_sssp_batch_info(h)
     # one at a time, same sources, checked against the batch rows
     ipg.ipg_sssp_dev(h, int(sources[0]), single, stream=stream)
     torch.cuda.synchronize()
@@ -698,7 +699,10 @@ def run_batch(a):
                 "one_at_a_time": {"value": round(world * k / (t_single / 1e3), 1), "unit": "queries/s",
                                   "ms_total": round(t_single, 2)},
                 "speedup": round(t_single / t_batch, 2), "results_equal": equal,
-                "supersteps": {"min": int(steps_b.min()), "max": int(steps_b.max())}}
+                "supersteps": {"min": int(steps_b.min()), "max": int(steps_b.max()),
+                               "sum_over_queries": int(steps_b.sum())},
+                "lane_loop": binfo,
+                "ms_per_lane_superstep": round(t_batch / max(binfo["supersteps"], 1), 3)}
         emit(line)
     h.destroy()
 

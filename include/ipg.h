@@ -257,6 +257,18 @@ ipg_status ipg_sssp_batch_dev(ipg_graph* g, const uint32_t* sources, uint32_t k,
                               uint32_t* supersteps_out, void* stream);
 
 /*
+ * Totals of the graph's last ipg_sssp_batch[_dev] call (a measurement aid; not
+ * in the paper): queries run, supersteps of the lane loop (each serves every
+ * lane holding a query), how many of them ran in pull form, supersteps after
+ * which finished lanes were harvested, and graph launches.  All zero before the
+ * first call.  IPG_EINVAL for NULL arguments.
+ */
+typedef struct {
+    uint64_t queries, supersteps, pull_supersteps, harvests, launches;
+} ipg_batch_info;
+ipg_status ipg_sssp_batch_info(const ipg_graph* g, ipg_batch_info* out);
+
+/*
  * ipg_sssp_noalloc — the same SSSP as ipg_sssp, for callers that may not
  * allocate device memory (the paper has no counterpart to this call).
  * Callers whose device memory belongs to another allocator (a framework's

@@ -426,7 +426,21 @@ def ipg_sssp_batch_dev(g: Graph, sources, dist_dev, stream=None):
     return steps
 
 
-__all__ += ["ipg_sssp_batch", "ipg_sssp_batch_dev"]
+__all__ += ["ipg_sssp_batch", "ipg_sssp_batch_dev", "ipg_sssp_batch_info"]
+
+
+class _CBatchInfo(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("queries", "supersteps", "pull_supersteps", "harvests", "launches")]
+
+
+def ipg_sssp_batch_info(g: "Graph") -> dict:
+    """Totals of the graph's last batched SSSP call (see include/ipg.h)."""
+    fn = load_library().ipg_sssp_batch_info
+    fn.argtypes = [ctypes.c_void_p, ctypes.POINTER(_CBatchInfo)]
+    fn.restype = ctypes.c_int
+    r = _CBatchInfo()
+    _check(fn(g.handle, ctypes.byref(r)))
+    return {k: int(getattr(r, k)) for k, _ in _CBatchInfo._fields_}
 
 
 def ipg_graph_create_batch(graphs, directed: bool) -> Graph:

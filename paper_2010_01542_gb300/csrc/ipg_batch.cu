@@ -101,6 +101,8 @@ struct BatchCtl {
     // output: rows of n distances in caller order
     uint32_t* out;
     unsigned long long out_stride;
+    // totals of the session (ipg_sssp_batch_info)
+    unsigned long long supersteps, pull_supersteps, harvests;
 };
 
 namespace {
@@ -499,6 +501,9 @@ __global__ void batch_step_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __r
     const unsigned finm = __ballot_sync(0xFFFFFFFFu, fin);
     if (fin && ctl->steps_out) ctl->steps_out[ctl->row[b]] = ctl->count[b];
     if (b == 0) {
+        ++ctl->supersteps;
+        if (!ctl->push) ++ctl->pull_supersteps;
+        if (finm) ++ctl->harvests;
         const uint32_t fn = ctr->next_size;
         uint32_t status = ctl->status | ctr->status;
         if (fn > n) status |= kStatusInternal;
@@ -575,6 +580,7 @@ struct BatchWorkspace {
     size_t list_cap = 0;
     unsigned long long* tasks = nullptr;  // push tasks of the current senders
     bool clean = false;                   // dist/sval all kInf, masks and counters zero
+    ipg_batch_info info{};                // totals of the last ipg_sssp_batch call
     cudaGraphExec_t loop[3] = {nullptr, nullptr, nullptr};  // superstep loop, per weight kind
 };
 
@@ -771,13 +777,19 @@ ipg_status sssp_batch_run(ipg_graph* g, const uint32_t* sources, uint32_t k, uin
     IPG_TRY(batch_session_begin(g, b, init, st));
     // every lane is refilled on the device: one launch per kLoopCap supersteps
     const uint64_t bound = ((uint64_t)k + kLanes) * ((uint64_t)g->n + 2) / kLoopCap + 2;
-    for (uint64_t launches = 0;; ++launches) {
+    uint64_t launches = 0;
+    for (;; ++launches) {
         if (launches > bound)
             return set_error(IPG_EDEVICE, "ipg_sssp_batch: the superstep loop did not end");
         IPG_TRY(batch_launch(g, b, st, "ipg_sssp_batch"));
         if (b->h_ctl->done) break;
     }
     b->clean = true;  // every lane was harvested
+    b->info.queries = k;
+    b->info.supersteps = b->h_ctl->supersteps;
+    b->info.pull_supersteps = b->h_ctl->pull_supersteps;
+    b->info.harvests = b->h_ctl->harvests;
+    b->info.launches = launches + 1;
     if (supersteps_out) {
         IPG_CUDA(cudaMemcpyAsync(supersteps_out, b->steps, sizeof(uint32_t) * k, cudaMemcpyDeviceToHost, st));
         IPG_CUDA(cudaStreamSynchronize(st));
@@ -849,6 +861,13 @@ void lanes_close(ipg_graph* g) {
 using namespace ipg;
 
 extern "C" {
+
+ipg_status ipg_sssp_batch_info(const ipg_graph* g, ipg_batch_info* out) {
+    if (!g || !out) return set_error(IPG_EINVAL, "ipg_sssp_batch_info: NULL argument");
+    const BatchWorkspace* b = (const BatchWorkspace*)g->batch;
+    *out = b ? b->info : ipg_batch_info{};
+    return IPG_OK;
+}
 
 ipg_status ipg_sssp_batch_dev(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_dev,
                               uint32_t* supersteps_out, void* stream) {

@@ -59,6 +59,7 @@ def test_pure_host_calls(lib):
     assert lib.ipg_graph_create(None, None, None, 0, 0, 1, None) == 1
     assert lib.ipg_graph_check_symmetric(None, None, None) == 1
     assert lib.ipg_graph_create_profile(None, None) == 1
+    assert lib.ipg_sssp_batch_info(None, None) == 1
 
 
 def test_header_is_valid_c(tmp_path):
