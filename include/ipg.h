@@ -505,9 +505,15 @@ void ipg_server_destroy(ipg_server* s);
  *                   per run) whenever no per-superstep timing is asked for and the
  *                   stats buffer holds at most 65536 records; 0 = the host drives
  *                   every superstep.  Default 1.
+ *   "pull_filter"   Hashmin/SSSP pull supersteps whose messages are below this
+ *                   percentage of m read a one-bit-per-vertex sender array before
+ *                   each gather and gather only from senders; 0 = never (default:
+ *                   measured slower on R-MAT 26/28), 100 = every pull superstep.
+ *   "batch_chunk"   batched SSSP: in-edges per warp task of the pull form (the
+ *                   engine's tile size), a multiple of 32 in [32, 65536].  Default 256.
  * Unknown names or invalid values return IPG_EINVAL.  Set knobs between calls,
  * not while a call runs.  A graph tuned by ipg_autotune uses its own values of
- * pull_divisor, batch_divisor, pr_engine and pr_carveout instead of these.
+ * pull_divisor, batch_divisor, batch_chunk, pr_engine and pr_carveout instead of these.
  */
 ipg_status ipg_set_tuning(const char* name, int64_t value);
 ipg_status ipg_get_tuning(const char* name, int64_t* value);
@@ -525,7 +531,9 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value);
  * Candidates, all of which give bit-identical results (min combiners are
  * order-free; both PageRank engines and every carveout add in one order):
  *   Hashmin, SSSP  pull_divisor in {0, 2, 4, 6, 10, 16, 32};
- *   batched SSSP   batch_divisor in {0, 2, 4, 6, 10, 16, 32};
+ *   batched SSSP   (batch_divisor, batch_chunk) in {(6, 256), (0, 256), (2, 256),
+ *                  (16, 256), (6, 128), (6, 512), (6, 1024)}: the push/pull switch
+ *                  and the tile size of the pull form (in-edges per warp task);
  *   PageRank       (pr_engine, pr_carveout) in {(0,-1), (0,60), (1,-1), (1,5)}.
  * Each candidate runs twice (the faster run counts): Hashmin and SSSP to
  * quiescence, batched SSSP on 32 sources (sssp_source and 31 caller ids spread
@@ -552,7 +560,7 @@ typedef struct {
     float hashmin_ms, sssp_ms, sssp_batch_ms, pagerank_ms;  /* best candidate's run, 0 if not timed */
     float hashmin_default_ms, sssp_default_ms, sssp_batch_default_ms, pagerank_default_ms;  /* process-wide knobs */
     uint32_t candidates_timed;  /* runs made by this call */
-    uint32_t reserved;
+    uint32_t sssp_batch_chunk;  /* batched SSSP: in-edges per warp task of its pull form (0 = not tuned) */
 } ipg_tune_report;
 
 ipg_status ipg_autotune(ipg_graph* g, uint32_t programs, uint32_t sssp_source, ipg_tune_report* report,

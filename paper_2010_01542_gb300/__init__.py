@@ -368,7 +368,7 @@ class _CTuneReport(ctypes.Structure):
                 ("pagerank_ms", ctypes.c_float), ("hashmin_default_ms", ctypes.c_float),
                 ("sssp_default_ms", ctypes.c_float), ("sssp_batch_default_ms", ctypes.c_float),
                 ("pagerank_default_ms", ctypes.c_float), ("candidates_timed", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("sssp_batch_chunk", ctypes.c_uint32)]
 
 
 def ipg_autotune(g: Graph, programs: int, sssp_source: int = INF, stream=None) -> dict:
@@ -379,7 +379,7 @@ def ipg_autotune(g: Graph, programs: int, sssp_source: int = INF, stream=None) -
     lib.ipg_autotune.restype = ctypes.c_int
     rep = _CTuneReport()
     _check(lib.ipg_autotune(g.handle, int(programs), int(sssp_source), ctypes.byref(rep), _stream_ptr(stream)))
-    return {name: getattr(rep, name) for name, _ in _CTuneReport._fields_ if name != "reserved"}
+    return {name: getattr(rep, name) for name, _ in _CTuneReport._fields_}
 
 
 __all__ += ["ipg_autotune", "IPG_TUNE_PAGERANK", "IPG_TUNE_HASHMIN", "IPG_TUNE_SSSP", "IPG_TUNE_SSSP_BATCH",

@@ -54,11 +54,7 @@ namespace ipg {
 namespace {
 
 constexpr int kLanes = 32;
-constexpr uint32_t kChunk = 256;  // in-edges per warp task
-#ifndef IPG_BATCH_UNROLL
-#define IPG_BATCH_UNROLL 4
-#endif
-constexpr int kUnroll = IPG_BATCH_UNROLL;  // sender lines in flight per warp
+constexpr int kUnroll = 4;  // sender lines in flight per warp (8 and 16 measured slower)
 
 constexpr unsigned kLoopCap = 1024;    // supersteps per graph launch
 constexpr uint32_t kPushChunk = 256;   // out-edges per push task
@@ -115,11 +111,11 @@ __device__ __forceinline__ uint32_t* fr_next(uint32_t* fr0, uint32_t* fr1, const
 }
 
 __global__ void chunk_rows_kernel(const uint64_t* __restrict__ off, uint32_t n, uint64_t m, uint64_t chunks,
-                                  uint32_t* __restrict__ chunk_row) {
+                                  uint32_t chunk, uint32_t* __restrict__ chunk_row) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += stride) {
-        // row holding edge c * kChunk: the last row whose start is <= that edge
-        const uint64_t e = c * kChunk;
+        // row holding edge c * chunk: the last row whose start is <= that edge
+        const uint64_t e = c * chunk;
         uint32_t lo = 0, hi = n;  // answer in [0, n - 1]
         while (lo + 1 < hi) {
             const uint32_t mid = (uint32_t)(((uint64_t)lo + hi) >> 1);
@@ -211,7 +207,7 @@ __device__ __forceinline__ void batch_flush(uint32_t v, uint32_t run, uint32_t l
 }
 
 // end of a row relative to the start of a chunk, clamped to 32 bits: a chunk holds at
-// most kChunk edges, so every value from kChunk up means "ends after this chunk"
+// most `chunk` edges, so every value from there up means "ends after this chunk"
 __device__ __forceinline__ uint32_t chunk_rel_end(uint64_t row_end, uint64_t e_begin) {
     const uint64_t r = row_end - e_begin;
     return r < 0xFFFFFFFFull ? (uint32_t)r : 0xFFFFFFFFu;
@@ -223,15 +219,15 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
     const uint32_t* __restrict__ w32, const uint32_t* __restrict__ chunk_row, uint64_t chunks, uint32_t n, uint64_t m,
     const uint32_t* __restrict__ sval, const uint32_t* __restrict__ smask, uint32_t* __restrict__ dist,
     uint32_t* __restrict__ cmask, uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl,
-    BatchCounters* __restrict__ ctr) {
+    BatchCounters* __restrict__ ctr, uint32_t chunk) {
     if (ctl->push) return;
     uint32_t* __restrict__ next = fr_next(fr0, fr1, ctl);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t c = warp; c < chunks; c += nwarps) {
-        const uint64_t e_begin = c * kChunk;
-        const uint32_t len = (uint32_t)(e_begin + kChunk < m ? kChunk : m - e_begin);
+        const uint64_t e_begin = c * chunk;
+        const uint32_t len = (uint32_t)(e_begin + chunk < m ? chunk : m - e_begin);
         uint32_t row = chunk_row[c];
         uint32_t bound = chunk_rel_end(csc_off[row + 1], e_begin);  // row end, relative to the chunk (may exceed len)
         uint32_t run = kInf;
@@ -569,7 +565,8 @@ struct BatchWorkspace {
     uint32_t* cmask = nullptr;  // [n]
     uint32_t* fr[2] = {nullptr, nullptr};
     uint32_t* chunk_row = nullptr;
-    uint64_t chunks = 0;
+    uint64_t chunks = 0, chunk_cap = 0;
+    uint32_t chunk = 0;  // in-edges per warp task of the pull form (0: not set up yet)
     BatchCounters* ctr = nullptr;
     BatchCtl* ctl = nullptr;
     BatchCtl* h_ctl = nullptr;            // pinned mirror
@@ -628,13 +625,35 @@ static ipg_status batch_prepare(ipg_graph* g, cudaStream_t st) {
     IPG_CUDA(cudaHostAlloc(&b->h_admit, sizeof(unsigned int), cudaHostAllocMapped));
     *b->h_admit = 0;
     IPG_CUDA(cudaHostGetDevicePointer((void**)&b->d_admit, b->h_admit, 0));
-    b->chunks = (g->m + kChunk - 1) / kChunk;
-    IPG_CUDA(cudaMalloc(&b->chunk_row, sizeof(uint32_t) * (b->chunks ? b->chunks : 1)));
-    if (b->chunks) {
-        chunk_rows_kernel<<<grid_for_warps(b->chunks / 32 + 1, sm_count_of(g->device)), 256, 0, st>>>(
-            g->csc_off, n, g->m, b->chunks, b->chunk_row);
+    return IPG_OK;
+}
+
+// The in-edge chunks of the pull form (the batched engine's tile size, a tuning knob):
+// their first rows are recomputed, and the loop graphs, which bake in the chunk
+// count, rebuilt, when the size changes.
+static ipg_status batch_chunks(ipg_graph* g, BatchWorkspace* b, cudaStream_t st) {
+    const uint32_t want = (uint32_t)batch_chunk_for(g);
+    if (b->chunk == want) return IPG_OK;
+    for (auto& x : b->loop)
+        if (x) {
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+    const uint64_t chunks = (g->m + want - 1) / want;
+    if (chunks > b->chunk_cap) {
+        cudaFree(b->chunk_row);
+        b->chunk_row = nullptr;
+        b->chunk_cap = 0;
+        IPG_CUDA(cudaMalloc(&b->chunk_row, sizeof(uint32_t) * (chunks ? chunks : 1)));
+        b->chunk_cap = chunks;
+    }
+    if (chunks) {
+        chunk_rows_kernel<<<grid_for_warps(chunks / 32 + 1, sm_count_of(g->device)), 256, 0, st>>>(
+            g->csc_off, g->n, g->m, chunks, want, b->chunk_row);
         IPG_CUDA(cudaGetLastError());
     }
+    b->chunks = chunks;
+    b->chunk = want;
     return IPG_OK;
 }
 
@@ -647,7 +666,7 @@ static void batch_superstep(ipg_graph* g, BatchWorkspace* b, int wkind, cudaGrap
 #define IPG_BATCH_PULL(K)                                                                                         \
     batch_pull_kernel<K><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,       \
                                                b->chunks, g->n, g->m, b->sval, b->smask, b->dist, b->cmask,      \
-                                               b->fr[0], b->fr[1], b->ctl, b->ctr)
+                                               b->fr[0], b->fr[1], b->ctl, b->ctr, b->chunk)
 #define IPG_BATCH_PUSH(K)                                                                                         \
     batch_push_kernel<K><<<fixed, 256, 0, st>>>(g->off, g->col, g->w8, g->w, b->tasks, b->sval, b->smask, b->dist,  \
                                                 b->cmask, b->fr[0], b->fr[1], b->ctl, b->ctr)
@@ -715,6 +734,7 @@ static int weight_kind(const ipg_graph* g) { return g->csc_w8 ? 1 : g->csc_w ? 2
 // session left them so), and the control block set for a new session.
 static ipg_status batch_session_begin(ipg_graph* g, BatchWorkspace* b, const BatchCtl& init, cudaStream_t st) {
     const size_t n = g->n;
+    IPG_TRY(batch_chunks(g, b, st));
     IPG_TRY(batch_loop_graph(g, b, weight_kind(g)));
     if (!b->clean) {
         IPG_CUDA(cudaMemsetAsync(b->dist, 0xFF, sizeof(uint32_t) * kLanes * n, st));

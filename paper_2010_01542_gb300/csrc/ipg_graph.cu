@@ -553,6 +553,8 @@ long long batch_divisor_for(const ipg_graph* g) {
     return g->tuned.batch ? g->tuned.batch_divisor : tuning().batch_divisor;
 }
 
+long long batch_chunk_for(const ipg_graph* g) { return g->tuned.batch ? g->tuned.batch_chunk : tuning().batch_chunk; }
+
 // ---------------------------------------------------------------------------
 // creation
 
@@ -1081,6 +1083,12 @@ ipg_status ipg_set_tuning(const char* name, int64_t value) {
         tuning().pull_filter = value;
         return IPG_OK;
     }
+    if (!strcmp(name, "batch_chunk")) {
+        if (value < 32 || value > 65536 || value % 32)
+            return set_error(IPG_EINVAL, "ipg_set_tuning: batch_chunk must be a multiple of 32 in [32, 65536]");
+        tuning().batch_chunk = value;
+        return IPG_OK;
+    }
     return set_error(IPG_EINVAL, "ipg_set_tuning: unknown knob '%s'", name);
 }
 
@@ -1116,6 +1124,10 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value) {
     }
     if (!strcmp(name, "pull_filter")) {
         *value = tuning().pull_filter;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "batch_chunk")) {
+        *value = tuning().batch_chunk;
         return IPG_OK;
     }
     return set_error(IPG_EINVAL, "ipg_get_tuning: unknown knob '%s'", name);

@@ -97,7 +97,7 @@ struct DeviceGuard {
 struct GraphTuning {
     bool pr = false, cc = false, sssp = false, batch = false;
     long long pr_engine = 0, pr_carveout = -1;
-    long long cc_divisor = 6, sssp_divisor = 6, batch_divisor = 6;
+    long long cc_divisor = 6, sssp_divisor = 6, batch_divisor = 6, batch_chunk = 256;
 };
 
 // per-superstep CUDA events (IPG_STAT_TIMING)
@@ -250,6 +250,7 @@ struct Tuning {
     long long push_loop = 1;     // Hashmin/SSSP: 1 = superstep loop in a CUDA graph where possible, 0 = host loop
     long long pr_engine = 0;     // PageRank pull kernel: 0 staged messages, 1 direct (registers)
     long long pull_filter = 0;   // Hashmin/SSSP pull: check sender bits first below this % of m messages; 0 = never
+    long long batch_chunk = 256; // batched SSSP pull: in-edges per warp task (the engine's tile size)
 };
 Tuning& tuning();
 // the graph's tuned value where it has one, else the process-wide knob
@@ -257,6 +258,7 @@ long long pull_divisor_for(const ipg_graph* g, bool sssp);
 long long pr_engine_for(const ipg_graph* g);
 long long pr_carveout_for(const ipg_graph* g);
 long long batch_divisor_for(const ipg_graph* g);
+long long batch_chunk_for(const ipg_graph* g);
 // stats helpers
 void stats_begin(ipg_stats* s);
 void stats_put(ipg_stats* s, uint32_t idx, const ipg_superstep_stats& rec);

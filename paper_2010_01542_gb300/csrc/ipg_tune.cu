@@ -16,6 +16,8 @@ namespace {
 constexpr int kSamples = 64;
 const long long kDivisors[] = {0, 2, 4, 6, 10, 16, 32};
 const long long kPrShapes[][2] = {{0, -1}, {0, 60}, {1, -1}, {1, 5}};  // (pr_engine, pr_carveout)
+// batched SSSP: (push/pull divisor, in-edges per warp task of the pull form: the tile size)
+const long long kBatchShapes[][2] = {{6, 256}, {0, 256}, {2, 256}, {16, 256}, {6, 128}, {6, 512}, {6, 1024}};
 
 __global__ void sample_offsets_kernel(const uint64_t* __restrict__ off, uint32_t n, uint64_t* __restrict__ out) {
     const uint32_t i = threadIdx.x;
@@ -45,13 +47,13 @@ void set_candidate(GraphTuning& t, int prog, long long a, long long b) {
     if (prog == kProgHashmin) t.cc = true, t.cc_divisor = a;
     if (prog == kProgSssp) t.sssp = true, t.sssp_divisor = a;
     if (prog == kProgPagerank) t.pr = true, t.pr_engine = a, t.pr_carveout = b;
-    if (prog == kProgBatch) t.batch = true, t.batch_divisor = a;
+    if (prog == kProgBatch) t.batch = true, t.batch_divisor = a, t.batch_chunk = b;
 }
 void copy_choice(GraphTuning& dst, const GraphTuning& src, int prog) {
     if (prog == kProgHashmin) set_candidate(dst, prog, src.cc_divisor, 0);
     if (prog == kProgSssp) set_candidate(dst, prog, src.sssp_divisor, 0);
     if (prog == kProgPagerank) set_candidate(dst, prog, src.pr_engine, src.pr_carveout);
-    if (prog == kProgBatch) set_candidate(dst, prog, src.batch_divisor, 0);
+    if (prog == kProgBatch) set_candidate(dst, prog, src.batch_divisor, src.batch_chunk);
 }
 
 std::mutex g_cache_mu;
@@ -178,10 +180,14 @@ ipg_status autotune(ipg_graph* g, uint32_t programs, uint32_t source, ipg_tune_r
             if (rc == IPG_OK) rc = best_of_two(st, &def_ms[prog], &r.candidates_timed, run);
             float best = -1.f;
             long long best_a = 0, best_b = 0;
-            const int count = prog == kProgPagerank ? 4 : (int)(sizeof(kDivisors) / sizeof(kDivisors[0]));
+            const int count = prog == kProgPagerank ? 4
+                              : prog == kProgBatch ? (int)(sizeof(kBatchShapes) / sizeof(kBatchShapes[0]))
+                                                   : (int)(sizeof(kDivisors) / sizeof(kDivisors[0]));
             for (int c = 0; c < count && rc == IPG_OK; ++c) {
-                const long long a = prog == kProgPagerank ? kPrShapes[c][0] : kDivisors[c];
-                const long long b = prog == kProgPagerank ? kPrShapes[c][1] : 0;
+                const long long a = prog == kProgPagerank ? kPrShapes[c][0]
+                                    : prog == kProgBatch  ? kBatchShapes[c][0]
+                                                          : kDivisors[c];
+                const long long b = prog == kProgPagerank ? kPrShapes[c][1] : prog == kProgBatch ? kBatchShapes[c][1] : 0;
                 set_candidate(g->tuned, prog, a, b);
                 float ms = 0.f;
                 rc = best_of_two(st, &ms, &r.candidates_timed, run);
@@ -211,7 +217,7 @@ ipg_status autotune(ipg_graph* g, uint32_t programs, uint32_t source, ipg_tune_r
                  (gt.batch ? IPG_TUNE_SSSP_BATCH : 0u);
     if (gt.cc) r.hashmin_pull_divisor = gt.cc_divisor;
     if (gt.sssp) r.sssp_pull_divisor = gt.sssp_divisor;
-    if (gt.batch) r.sssp_batch_divisor = gt.batch_divisor;
+    if (gt.batch) r.sssp_batch_divisor = gt.batch_divisor, r.sssp_batch_chunk = (uint32_t)gt.batch_chunk;
     if (gt.pr) r.pr_engine = gt.pr_engine, r.pr_carveout = gt.pr_carveout;
     r.hashmin_ms = best_ms[kProgHashmin], r.hashmin_default_ms = def_ms[kProgHashmin];
     r.sssp_ms = best_ms[kProgSssp], r.sssp_default_ms = def_ms[kProgSssp];

@@ -194,3 +194,16 @@ def test_batch_long_paths_span_several_graph_launches(ipg):
     sources = np.array([0, 1, 5, 150, 299, 0])
     dist, steps = _check_batch(ipg, g, sources, g.weights, use_oracle=True)
     assert steps.max() > 3 * 64
+
+
+@pytest.mark.parametrize("chunk", [32, 128, 1024, 4096])
+def test_batch_chunk_sizes_give_the_same_rows(ipg, chunk):
+    """The pull form's tile size (in-edges per warp task) changes no row or count."""
+    g = gen.rmat(12, 16, seed=12, weighted=True)
+    sources = np.random.default_rng(12).integers(0, g.n, size=45)
+    old = ipg.ipg_get_tuning("batch_chunk")
+    try:
+        ipg.ipg_set_tuning("batch_chunk", chunk)
+        _check_batch(ipg, g, sources, g.weights)
+    finally:
+        ipg.ipg_set_tuning("batch_chunk", old)

@@ -65,6 +65,7 @@ def test_autotune_keeps_results(ipg, name, spec):
     rep = ipg.ipg_autotune(h, progs | ipg.IPG_TUNE_FORCE, src)
     assert rep["programs"] == progs and rep["cached"] == 0 and rep["candidates_timed"] > 0
     assert rep["sssp_pull_divisor"] in DIVISORS and rep["sssp_batch_divisor"] in DIVISORS
+    assert rep["sssp_batch_chunk"] in (128, 256, 512, 1024)
     assert rep["sssp_batch_ms"] > 0
     assert (rep["pr_engine"], rep["pr_carveout"]) in PR_SHAPES
     if hashmin:
@@ -82,7 +83,8 @@ def test_autotune_keeps_results(ipg, name, spec):
     h2 = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, not spec["undirected"])
     rep2 = ipg.ipg_autotune(h2, progs, src)
     assert rep2["cached"] == 1 and rep2["candidates_timed"] == 0
-    for k in ("sssp_pull_divisor", "sssp_batch_divisor", "pr_engine", "pr_carveout", "hashmin_pull_divisor"):
+    for k in ("sssp_pull_divisor", "sssp_batch_divisor", "sssp_batch_chunk", "pr_engine", "pr_carveout",
+              "hashmin_pull_divisor"):
         assert rep2[k] == rep[k], k
     after2 = _results(ipg, h2, g, src, hashmin)
     after2["batch"], after2["batch_steps"] = ipg.ipg_sssp_batch(h2, batch_src)
