@@ -346,6 +346,29 @@ def measured_traffic(kernel, workload):
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
+def host_huge_fraction(arrays):
+    """Fraction of the bytes of these host arrays that the kernel backs with transparent huge
+    pages (AnonHugePages of the mappings holding them, from /proc/self/smaps); None if unknown."""
+    try:
+        spans = [(a.ctypes.data, a.ctypes.data + a.nbytes) for a in arrays if a is not None and a.nbytes]
+        total = sum(e - b for b, e in spans)
+        huge = 0
+        cur = None
+        for line in open("/proc/self/smaps"):
+            head = line.split()
+            if head and "-" in head[0] and len(head) >= 5 and all(c in "0123456789abcdef-" for c in head[0]):
+                lo, hi = (int(x, 16) for x in head[0].split("-"))
+                cur = (lo, hi) if any(b < hi and e > lo for b, e in spans) else None
+            elif cur and line.startswith("AnonHugePages:"):
+                kb = int(line.split()[1])
+                lo, hi = cur
+                inside = sum(max(0, min(e, hi) - max(b, lo)) for b, e in spans)
+                huge += min(kb * 1024, inside)
+        return round(huge / total, 4) if total else None
+    except Exception:  # noqa: BLE001 - a diagnostic only
+        return None
+
+
 def peak_hbm():
     try:
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -500,6 +523,7 @@ def run_ours(a):
                "d2h_bytes_per_step": int(out_r.nbytes + out_d.nbytes), "ms_per_step": round(t_e2e * 1e3, 2),
                "phases_ms": {k: round(statistics.mean(v) * 1e3, 1) for k, v in phases.items()},
                "create_ms": {k: round(statistics.mean(p[k] for p in create_parts), 1) for k in create_parts[0]},
+               "host_huge_page_fraction": host_huge_fraction([host.offsets, host.cols, host.weights]),
                "api": "ipg_graph_create + ipg_autotune (cached) + ipg_pagerank + ipg_sssp + ipg_graph_destroy, "
                       "host buffers"}
 

@@ -10,12 +10,20 @@
 //
 // These buffers are anonymous mappings aligned to the transparent huge page size and
 // advised MADV_HUGEPAGE before their first touch, so the kernel backs them with huge
-// pages where it can (compacting memory if it must), and then registered with
-// cudaHostRegister (portable to every context).  Small requests (below one huge page)
+// pages where it can (compacting memory if it must).  Where the page faults still got
+// base pages (memory fragmented by earlier processes), MADV_COLLAPSE asks the kernel
+// to gather them into huge pages synchronously; kernels without it ignore the request.
+// The buffers are then registered with cudaHostRegister (portable to every context).
+// On one box, after the GPU test suite, an upload from base-page buffers ran at
+// 14.5 GB/s against 170-210 GB/s from huge pages.  Small requests (below one huge page)
 // are page aligned only.  Where the kernel has no transparent huge pages the advice is
 // ignored and the buffer is an ordinary page-locked mapping.
 #include <sys/mman.h>
 #include <unistd.h>
+
+#ifndef MADV_COLLAPSE
+#define MADV_COLLAPSE 25  // Linux 6.1: collapse the range into transparent huge pages now
+#endif
 
 #include <cstdint>
 #include <cstdio>
@@ -83,6 +91,7 @@ extern "C" ipg_status ipg_host_alloc(size_t bytes, void** out) {
         madvise(p, len, MADV_HUGEPAGE);  // advice only: ignored where the kernel has no THP
         // first touch with one write per huge page, so each fault can take a whole huge page
         for (size_t off = 0; off < len; off += granule) static_cast<volatile char*>(p)[off] = 0;
+        madvise(p, len, MADV_COLLAPSE);  // best effort; an error leaves the pages as they are
     }
     cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterPortable);
     if (e != cudaSuccess) {

@@ -158,24 +158,29 @@ def test_cancel_queued_queries(ipg):
 def test_queries_join_a_running_lane_session(ipg):
     """SSSP queries submitted while a lane session runs on the graph are seeded into free
     lanes at superstep boundaries (completion.joined == 1); every result equals the oracle's
-    and the query run alone, whichever superstep it joined at."""
+    and the query run alone, whichever superstep it joined at.  The single worker is first
+    kept busy by a long PageRank on another graph, so the first SSSP queries queue up and
+    start a session; the rest arrive while it runs."""
     import time
 
     import oracle
 
     g = gen.rmat(15, 16, seed=31, undirected=True, weighted=True)
+    big = gen.rmat(16, 16, seed=32, undirected=True, weighted=True)
     h = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, False)
+    hb = ipg.ipg_graph_create(big.offsets, big.cols, big.weights, big.n, big.m, False)
     rng = np.random.default_rng(31)
     sources = [int(x) for x in rng.integers(0, g.n, size=120)]
-    srv = ipg.Server([h], workers=1, min_sssp_batch=4, prepare=True)
+    srv = ipg.Server([h, hb], workers=1, min_sssp_batch=4, prepare=True)
+    srv.submit(1, ipg.IPG_Q_PAGERANK, np.empty(big.n, dtype=np.float32), updates=200, user=10_000)
     outs = {}
     for u, src in enumerate(sources):
         outs[u] = np.empty(g.n, dtype=np.uint32)
         srv.submit(0, ipg.IPG_Q_SSSP, outs[u], source=src, user=u)
-        if u >= 8:
-            time.sleep(0.0005)  # later queries arrive while the first ones run
+        if u >= 8 and u % 2 == 0:
+            time.sleep(0.001)  # later queries arrive while the session runs
     srv.drain()
-    done = srv.poll(0)
+    done = [c for c in srv.poll(0) if c.user != 10_000]
     srv.close()
     assert len(done) == len(sources)
     joined = 0
