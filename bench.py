@@ -76,7 +76,22 @@ def parse():
                    help="Hashmin/SSSP direction knob (library default if omitted; 0 = always push)")
     p.add_argument("--no-autotune", action="store_true",
                    help="skip ipg_autotune (the graph then runs with the process-wide knobs)")
+    p.add_argument("--tuning", action="append", default=[], metavar="NAME=VALUE",
+                   help="set a library knob (ipg_set_tuning) before the run, e.g. batch_loop=0 for a "
+                        "launch list in which every kernel of the batched loop is visible; repeatable")
     return p.parse_args()
+
+
+def apply_tuning(a):
+    """--tuning NAME=VALUE: process-wide library knobs, set before anything runs."""
+    if not a.tuning:
+        return
+    import paper_2010_01542_gb300 as ipg
+
+    ipg.load_library()
+    for item in a.tuning:
+        name, _, value = item.partition("=")
+        ipg.ipg_set_tuning(name.strip(), int(value))
 
 
 _CAPTURE = None  # a list while the default run collects the other workloads' lines
@@ -1119,7 +1134,9 @@ def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    elif a.workload in ("pagerank16", "hashmin20"):
+        return
+    apply_tuning(a)
+    if a.workload in ("pagerank16", "hashmin20"):
         run_small_config(a, a.workload)
     elif a.workload == "batch":
         run_batch(a)

@@ -241,15 +241,20 @@ ipg_status ipg_sssp_dev(ipg_graph* g, uint32_t source, uint32_t* dist_dev, ipg_s
 /*
  * ipg_sssp_batch — k independent SSSP runs, each exactly as ipg_sssp from
  * sources[i], executed together on one graph (batched queries; not in the
- * paper, whose runs are one source at a time).  Groups of 32 sources share each
- * superstep: the 32 values of a vertex sit in one 128-byte line, so one
- * coalesced read per in-edge serves the whole group.
+ * paper, whose runs are one source at a time).  Up to 256 queries share each
+ * superstep, in lines of 32: the 32 values of a line of a vertex sit in one
+ * 128-byte line of memory, so one coalesced read per in-edge and line serves 32
+ * queries.  The queries start together, those whose source has out-edges first,
+ * in the fewest lines (1, 2, 4 or 8) that hold them; further queries take the
+ * lanes that finish.
  *   sources         host, k vertex ids < n (repeats allowed), else IPG_EINVAL;
  *   dist_out        host, k * n uint32: row i holds the distances from sources[i]
  *                   (UINT32_MAX = unreachable);
  *   supersteps_out  host, k entries or NULL: the superstep count of each run.
  * ipg_sssp_batch_dev writes the k * n result to device memory on `stream`.
- * Uses 2 x 128 bytes per vertex of device workspace, kept with the graph.
+ * Uses about 264 bytes per vertex and line of device workspace, kept with the
+ * graph (fewer lines are used when that would not fit in three quarters of free
+ * device memory); ipg_sssp_batch also stages up to 256 rows of n words.
  */
 ipg_status ipg_sssp_batch(ipg_graph* g, const uint32_t* sources, uint32_t k, uint32_t* dist_out,
                           uint32_t* supersteps_out);
@@ -260,11 +265,12 @@ ipg_status ipg_sssp_batch_dev(ipg_graph* g, const uint32_t* sources, uint32_t k,
  * Totals of the graph's last ipg_sssp_batch[_dev] call (a measurement aid; not
  * in the paper): queries run, supersteps of the lane loop (each serves every
  * lane holding a query), how many of them ran in pull form, supersteps after
- * which finished lanes were harvested, and graph launches.  All zero before the
- * first call.  IPG_EINVAL for NULL arguments.
+ * which finished lanes were harvested, graph launches, and the lanes the call
+ * used (32 per line).  All zero before the first call.  IPG_EINVAL for NULL
+ * arguments.
  */
 typedef struct {
-    uint64_t queries, supersteps, pull_supersteps, harvests, launches;
+    uint64_t queries, supersteps, pull_supersteps, harvests, launches, lanes;
 } ipg_batch_info;
 ipg_status ipg_sssp_batch_info(const ipg_graph* g, ipg_batch_info* out);
 
@@ -511,6 +517,11 @@ void ipg_server_destroy(ipg_server* s);
  *                   measured slower on R-MAT 26/28), 100 = every pull superstep.
  *   "batch_chunk"   batched SSSP: in-edges per warp task of the pull form (the
  *                   engine's tile size), a multiple of 32 in [32, 65536].  Default 256.
+ *   "batch_loop"    batched SSSP: 1 = the superstep loop runs on the device inside a
+ *                   CUDA graph (one host synchronisation per 1024 supersteps); 0 = the
+ *                   host launches every superstep's kernels and reads the loop state
+ *                   back after each (for profilers that do not follow kernels inside
+ *                   conditional graph nodes).  Results are the same.  Default 1.
  * Unknown names or invalid values return IPG_EINVAL.  Set knobs between calls,
  * not while a call runs.  A graph tuned by ipg_autotune uses its own values of
  * pull_divisor, batch_divisor, batch_chunk, pr_engine and pr_carveout instead of these.

@@ -430,7 +430,7 @@ __all__ += ["ipg_sssp_batch", "ipg_sssp_batch_dev", "ipg_sssp_batch_info"]
 
 
 class _CBatchInfo(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_uint64) for k in ("queries", "supersteps", "pull_supersteps", "harvests", "launches")]
+    _fields_ = [(k, ctypes.c_uint64) for k in ("queries", "supersteps", "pull_supersteps", "harvests", "launches", "lanes")]
 
 
 def ipg_sssp_batch_info(g: "Graph") -> dict:

@@ -1089,6 +1089,11 @@ ipg_status ipg_set_tuning(const char* name, int64_t value) {
         tuning().batch_chunk = value;
         return IPG_OK;
     }
+    if (!strcmp(name, "batch_loop")) {
+        if (value != 0 && value != 1) return set_error(IPG_EINVAL, "ipg_set_tuning: batch_loop must be 0 or 1");
+        tuning().batch_loop = value;
+        return IPG_OK;
+    }
     return set_error(IPG_EINVAL, "ipg_set_tuning: unknown knob '%s'", name);
 }
 
@@ -1128,6 +1133,10 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value) {
     }
     if (!strcmp(name, "batch_chunk")) {
         *value = tuning().batch_chunk;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "batch_loop")) {
+        *value = tuning().batch_loop;
         return IPG_OK;
     }
     return set_error(IPG_EINVAL, "ipg_get_tuning: unknown knob '%s'", name);

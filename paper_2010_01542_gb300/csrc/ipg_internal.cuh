@@ -251,6 +251,7 @@ struct Tuning {
     long long pr_engine = 0;     // PageRank pull kernel: 0 staged messages, 1 direct (registers)
     long long pull_filter = 0;   // Hashmin/SSSP pull: check sender bits first below this % of m messages; 0 = never
     long long batch_chunk = 256; // batched SSSP pull: in-edges per warp task (the engine's tile size)
+    long long batch_loop = 1;    // batched SSSP: 1 = superstep loop in a CUDA graph, 0 = launched from the host
 };
 Tuning& tuning();
 // the graph's tuned value where it has one, else the process-wide knob

@@ -124,8 +124,8 @@ size_t workspace_need(const ipg_graph* g, uint32_t kind, uint32_t k, uint32_t mi
     } else {
         if (!g->stamp) need += n * 36 + tiles * 4;
         if (!g->sval) need += n * 4 + tiles * 12;
-        // batched SSSP: dist and sender rows [n][32], masks, frontiers, push tasks, chunk rows
-        if (kind == IPG_Q_SSSP && k >= min_batch && !g->batch) need += n * 280 + (m / 256 + 1) * 12;
+        // batched SSSP (one line): dist and sender rows [n][32], masks, frontiers, push tasks, chunk rows
+        if (kind == IPG_Q_SSSP && k >= min_batch && !g->batch) need += n * 288 + (m / 256 + 1) * 12;
     }
     if (!g->val_stage) need += n * 4;
     return need;

@@ -207,3 +207,107 @@ def test_batch_chunk_sizes_give_the_same_rows(ipg, chunk):
         _check_batch(ipg, g, sources, g.weights)
     finally:
         ipg.ipg_set_tuning("batch_chunk", old)
+
+
+def _lines_for(g, sources):
+    sending = int((g.out_degree()[np.asarray(sources)] > 0).sum())
+    lines = 1
+    while lines < 8 and lines * 32 < sending:
+        lines *= 2
+    return lines
+
+
+@pytest.mark.parametrize("k", [33, 70, 140, 300])
+def test_batch_wide_lines(ipg, k):
+    """More than 32 queries run in 2, 4 or 8 lines of 32 lanes; beyond 256 the lanes
+    that finish take the rest.  Sources without out-edges are listed after the others,
+    so every row must still land in its own output row.  u8, u32 and unit weights."""
+    rng = np.random.default_rng(900 + k)
+    g = gen.random_multigraph(3000, 24000, seed=k, weighted=True)
+    zero = np.nonzero(g.out_degree() == 0)[0]
+    sources = rng.integers(0, g.n, size=k)
+    if zero.size:
+        sources[::7] = zero[rng.integers(0, zero.size, size=sources[::7].size)]
+    sources[1] = sources[0]  # a repeated source
+    wide = rng.integers(1, 70000, size=g.m).astype(np.uint32)
+    import torch
+
+    for weights in (g.weights, wide, None):
+        h = ipg.ipg_graph_create(g.offsets, g.cols, weights, g.n, g.m, True)
+        # the device entry runs all k in one call (the host entry stages groups of 256)
+        d = torch.empty(k * g.n, dtype=torch.int32, device="cuda")
+        steps = ipg.ipg_sssp_batch_dev(h, sources, d)
+        torch.cuda.synchronize()
+        dist = d.cpu().numpy().view(np.uint32).reshape(k, g.n)
+        info = ipg.ipg_sssp_batch_info(h)
+        assert info["queries"] == k and info["lanes"] == 32 * _lines_for(g, sources), info
+        for i in list(range(0, k, 5)) + [1, k - 1]:
+            ref, cnt, _ = ipg.ipg_sssp(h, int(sources[i]))
+            np.testing.assert_array_equal(dist[i], ref, err_msg=f"row {i} source {sources[i]}")
+            assert steps[i] == cnt
+        for i in (0, 2, k // 2):
+            o = oracle.sssp(g.n, g.offsets, g.cols, weights, int(sources[i]))
+            np.testing.assert_array_equal(dist[i], o.values)
+            assert steps[i] == o.supersteps
+
+
+def test_batch_wide_then_one_line_on_one_graph(ipg):
+    """A graph whose workspace grew to 8 lines serves a one-line call next, and the
+    reverse: the value arrays are re-laid out between calls without stale values."""
+    g = gen.rmat(11, 16, seed=21, weighted=True)
+    rng = np.random.default_rng(21)
+    h = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, True)
+    few = rng.integers(0, g.n, size=9)
+    many = rng.integers(0, g.n, size=250)
+    for sources in (few, many, few, many[:40]):
+        dist, steps = ipg.ipg_sssp_batch(h, sources)
+        for i in range(0, len(sources), 3):
+            ref, cnt, _ = ipg.ipg_sssp(h, int(sources[i]))
+            np.testing.assert_array_equal(dist[i], ref)
+            assert steps[i] == cnt
+
+
+@pytest.mark.parametrize("first_weight", [0xFFFFFF00, 0xFFFFFFFF])
+def test_batch_wide_overflow_is_reported(ipg, first_weight):
+    """A path length that would reach UINT32_MAX fails the whole batched call with
+    IPG_EOVERFLOW in the wide engine too (40 sending queries: two lines of lanes),
+    whether the first message already overflows or the second one does."""
+    n = 50
+    src = [0, 1] + list(range(3, 43))
+    dst = [1, 2] + [44] * 40
+    w = [first_weight, 0xFFFFFF00] + [1] * 40
+    g = gen.csr_from_edges(n, np.array(src), np.array(dst), weights=np.array(w, dtype=np.uint32))
+    h = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, n, g.m, True)
+    sources = [0] + list(range(3, 43))
+    with pytest.raises(ipg.IpgError) as e:
+        ipg.ipg_sssp_batch(h, sources)
+    assert e.value.status == 7
+    # without the overflowing source the same graph runs
+    dist, steps = ipg.ipg_sssp_batch(h, sources[1:])
+    assert ipg.ipg_sssp_batch_info(h)["lanes"] == 64
+    for i, s in enumerate(sources[1:]):
+        ref, cnt, _ = ipg.ipg_sssp(h, s)
+        np.testing.assert_array_equal(dist[i], ref)
+        assert steps[i] == cnt
+
+
+@pytest.mark.parametrize("k", [20, 150])
+def test_batch_host_driven_loop_gives_the_same_rows(ipg, k):
+    """batch_loop 0 launches every superstep's kernels from the host instead of the
+    graph's WHILE node; one and eight lines give the same rows and counts."""
+    g = gen.rmat(12, 16, seed=31, weighted=True)
+    sources = np.random.default_rng(31 + k).integers(0, g.n, size=k)
+    h = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, True)
+    ref, ref_steps = ipg.ipg_sssp_batch(h, sources)
+    old = ipg.ipg_get_tuning("batch_loop")
+    try:
+        ipg.ipg_set_tuning("batch_loop", 0)
+        dist, steps = ipg.ipg_sssp_batch(h, sources)
+    finally:
+        ipg.ipg_set_tuning("batch_loop", old)
+    np.testing.assert_array_equal(dist, ref)
+    np.testing.assert_array_equal(steps, ref_steps)
+    for i in range(0, k, 7):
+        o, cnt, _ = ipg.ipg_sssp(h, int(sources[i]))
+        np.testing.assert_array_equal(dist[i], o)
+        assert steps[i] == cnt

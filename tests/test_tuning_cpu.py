@@ -24,6 +24,7 @@ KNOBS = {
     "push_loop": ([0, 1], [2, -1]),
     "pull_filter": ([0, 60, 100], [-1, 101]),
     "batch_chunk": ([32, 128, 256, 1024, 65536], [0, 16, 100, 65568]),
+    "batch_loop": ([0, 1], [2, -1]),
 }
 
 
