@@ -61,7 +61,7 @@ def parse():
     p.add_argument("--requests", type=int, default=10000, help="serve: measured requests (after 10%% warm-up)")
     p.add_argument("--batch-sources", type=int, default=256)
     p.add_argument("--min-sssp-batch", type=int, default=0,
-                   help="serve: fewest queued SSSP queries that start a lane session (0: the library default)")
+                   help="serve: fewest queued SSSP queries that start a lane session (0: the library default, per graph)")
     p.add_argument("--scale", type=int, default=26)
     p.add_argument("--edge-factor", type=int, default=28)
     p.add_argument("--seed", type=int, default=1)

@@ -394,9 +394,11 @@ ipg_status ipg_combine_dev(int kind, uint32_t n, const uint32_t* dst_dev, const 
 /*
  * Serving (not in the paper): a resident set of graphs answering a stream of
  * queries with continuous batching.  Worker threads take the graph whose head
- * query has waited longest (one worker per graph at a time); all of its queued
- * SSSP queries run together (ipg_sssp_batch), which lets queries that arrived
- * while the previous dispatch was on the GPU join the next one; queued Hashmin
+ * query has waited longest (one worker per graph at a time).  SSSP queries at
+ * the head of a graph's queue run one source at a time, or, from
+ * min_sssp_batch queued queries on, in a lane session of the batched engine
+ * (32 lanes): queries that arrive while the session is on the GPU take lanes
+ * that free up, at the next superstep boundary (continuous batching); queued Hashmin
  * queries (or PageRank queries with the same update count) on one graph share
  * one run, as they compute the same result (in flight only: completed results
  * are never reused).  Different graphs run concurrently on their own
@@ -440,7 +442,8 @@ typedef struct {
     uint32_t max_batch;         /* SSSP queries dispatched together at most; 0 -> 256 */
     uint64_t workspace_budget;  /* bytes of graph workspace held at once; 0 -> free memory */
     uint64_t reserve_bytes;     /* device memory kept free when budget is 0; 0 -> 1 GiB */
-    uint32_t min_sssp_batch;    /* fewer queued SSSP queries run one source at a time; 0 -> 16 */
+    uint32_t min_sssp_batch;    /* fewer queued SSSP queries run one source at a time; 0 -> per
+                                   graph, 3 * 2^(0.375 * (log2 m - 18)) clamped to [2, 32] */
     uint32_t flags;             /* IPG_SERVER_* bits */
 } ipg_server_options;
 

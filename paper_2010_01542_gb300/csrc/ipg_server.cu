@@ -5,11 +5,12 @@
 // waiting graph that no other worker is running (calls on one graph share its
 // workspace and must not overlap) and dispatch:
 //   - SSSP queries at the head of the graph's queue: with at least
-//     min_sssp_batch of them queued (16 by default) a lane session of the
-//     batched engine starts: each query takes one of 32 lanes, and whenever a
-//     lane's query finishes (its run quiesced) the lane is harvested and the next
-//     SSSP query at the head of the queue takes it at the following superstep
-//     boundary, so queries that arrive while others are on the GPU join the
+//     min_sssp_batch of them queued (by default 2 to 32, growing with the graph's
+//     edge count) a lane session of the batched engine starts: each query takes
+//     one of 32 lanes, and whenever a lane's query finishes (its run quiesced)
+//     the lane is harvested and the next SSSP query at the head of the queue
+//     takes it at the following superstep boundary, so queries that arrive
+//     while others are on the GPU join the
 //     running batch (continuous batching).  A submit for a graph in a session
 //     raises a flag in mapped host memory that ends the running graph launch at
 //     the next superstep boundary when a lane is free.  The session admits no
@@ -27,6 +28,7 @@
 // the caller's host buffers; completions carry timestamps for latency.  A query
 // can be cancelled until a worker dispatches it.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -62,7 +64,7 @@ struct ipg_server {
     size_t budget = 0;  // 0: use free device memory minus reserve
     size_t reserve = 0;
     uint32_t max_batch = 256;
-    uint32_t min_batch = 16;  // fewer queued SSSP queries run one source at a time
+    uint32_t min_batch = 0;   // fewer queued SSSP queries run one source at a time (0: per graph)
     size_t stage_words = 0;   // per-worker staging allocated at start (IPG_SERVER_PREPARE)
     std::chrono::steady_clock::time_point t0;
     int device = 0;
@@ -78,11 +80,19 @@ void release_workspace(ipg_graph* g);  // ipg_graph.cu
 
 namespace {
 
-// default for ipg_server_options.min_sssp_batch: fewer queued SSSP queries than this
-// run one source at a time.  A batched group costs about as much whatever its
-// size up to 32 sources (29 ms on R-MAT 22/16 against 1.7 ms per one-source run),
-// so batching pays from about 16 queued queries.
-constexpr uint32_t kMinSsspBatch = 16;
+// Default for ipg_server_options.min_sssp_batch, per graph: fewer queued SSSP
+// queries than this run one source at a time.  A lane session's dense supersteps
+// scan every in-edge once for all its lanes, so it pays from fewer queries on a
+// smaller graph, whose one-source runs are launch-bound.  Measured crossovers of
+// ipg_sssp_batch against one-at-a-time runs on directed R-MAT graphs (EF 16): about
+// 3 queries at m = 2.6e5, 6 at m = 4.2e6 and 26 at m = 6.5e7; this follows
+// 3 * 2^(0.375 * (log2 m - 18)) between 2 and 32.
+uint32_t session_threshold(const ipg_server* s, const ipg_graph* g) {
+    if (s->min_batch) return s->min_batch;
+    const double lg = g->m > 1 ? std::log2((double)g->m) : 0.0;
+    const double k = 3.0 * std::exp2(0.375 * (lg - 18.0));
+    return k < 2.0 ? 2u : k > 32.0 ? 32u : (uint32_t)std::lround(k);
+}
 
 // one run of every program on every graph, so their workspaces exist before serving
 ipg_status prepare_graphs(ipg_graph* const* graphs, uint32_t count) {
@@ -313,7 +323,8 @@ void worker_main(ipg_server* s) {
         const uint32_t kind = slot.pending.front().q.kind;
         size_t head_sssp = 0;  // SSSP queries at the head of the queue
         for (auto it = slot.pending.begin(); it != slot.pending.end() && it->q.kind == IPG_Q_SSSP; ++it) ++head_sssp;
-        const bool session = kind == IPG_Q_SSSP && head_sssp >= s->min_batch && s->max_batch > 1;
+        const uint32_t min_batch = session_threshold(s, slot.g);
+        const bool session = kind == IPG_Q_SSSP && head_sssp >= min_batch && s->max_batch > 1;
         if (session) {
             const size_t cap = std::min<size_t>(32, s->max_batch);
             while (batch.size() < cap && !slot.pending.empty() && slot.pending.front().q.kind == IPG_Q_SSSP) {
@@ -343,8 +354,7 @@ void worker_main(ipg_server* s) {
             }
         }
         // admission by device memory
-        const size_t need = workspace_need(slot.g, kind, session ? s->min_batch : (uint32_t)batch.size(),
-                                           s->min_batch);
+        const size_t need = workspace_need(slot.g, kind, session ? min_batch : (uint32_t)batch.size(), min_batch);
         for (;;) {
             size_t avail;
             if (s->budget) {
@@ -445,7 +455,7 @@ ipg_status ipg_server_create(ipg_graph* const* graphs, uint32_t count, const ipg
     s->max_batch = opt && opt->max_batch ? opt->max_batch : 256;
     s->budget = opt ? (size_t)opt->workspace_budget : 0;
     s->reserve = opt && opt->reserve_bytes ? (size_t)opt->reserve_bytes : ((size_t)1 << 30);
-    s->min_batch = opt && opt->min_sssp_batch ? opt->min_sssp_batch : kMinSsspBatch;
+    s->min_batch = opt && opt->min_sssp_batch ? opt->min_sssp_batch : 0u;
     if (opt && (opt->flags & IPG_SERVER_PREPARE)) {
         const ipg_status r = prepare_graphs(graphs, count);
         if (r != IPG_OK) {
