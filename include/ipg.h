@@ -245,7 +245,7 @@ ipg_status ipg_sssp_dev(ipg_graph* g, uint32_t source, uint32_t* dist_dev, ipg_s
  * superstep, in lines of 32: the 32 values of a line of a vertex sit in one
  * 128-byte line of memory, so one coalesced read per in-edge and line serves 32
  * queries.  The queries start together, those whose source has out-edges first,
- * in the fewest lines (1, 2, 4 or 8) that hold them; further queries take the
+ * in the fewest lines (1 to 8) that hold them; further queries take the
  * lanes that finish.
  *   sources         host, k vertex ids < n (repeats allowed), else IPG_EINVAL;
  *   dist_out        host, k * n uint32: row i holds the distances from sources[i]

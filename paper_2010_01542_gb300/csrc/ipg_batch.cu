@@ -1,12 +1,12 @@
 // Batched SSSP: many sources on one graph, each an independent synchronous
 // Pregel SSSP (Sec. VI-C), run together superstep by superstep.
 //
-// The engine has 32 * V lanes (V = 1, 2, 4 or 8 lines of 32), one query (a
-// source) per lane or none.  Values live vertex-major, dist[v][line][lane], so
-// the 32 lanes of one line of a vertex are one 128-byte line of memory: in a
-// pull superstep every in-edge (u -> v) costs one read per line of u's sender
-// values that holds a sender, where 32 V separate runs would each pay a random
-// 4-byte gather.  A superstep:
+// The engine has 32 * L lanes (L = 1 to 8 lines of 32), one query (a source) per
+// lane or none.  Values live vertex-major, dist[v][line][lane] with rows of L
+// lines, so the 32 lanes of one line of a vertex are one 128-byte line of memory:
+// in a pull superstep every in-edge (u -> v) costs one read per line of u's
+// sender values that holds a sender, where 32 L separate runs would each pay a
+// random 4-byte gather.  A superstep:
 //   refill   free lanes take the next queries (from a device list of sources, or
 //            from seeds the host wrote at a superstep boundary): the source's
 //            value becomes 0 and it joins the current senders;
@@ -35,13 +35,14 @@
 // it joined at.
 //
 // Which vertices send is kept per line: smask[u][j] holds the sending lanes of
-// line j, and with V > 1 sany[u] holds one bit per line that has a sender (the
+// line j, and with L > 1 sany[u] holds one bit per line that has a sender (the
 // pull form gathers that word per in-edge and loads only the lines it names).
 // With one line, a warp folds each active edge with its 32 lanes, the lanes
 // that do not send from the source skipping their load.  With more, each thread
-// holds V lanes of a row (one or two 16-byte vectors), and the rows of the next
-// edges are staged in a per-warp ring in shared memory by cp.async, so that a
-// warp keeps several rows in flight without holding them in registers.
+// holds V lanes of a row (V = 2, 4 or 8, the next of L: one or two vectors of 8
+// or 16 bytes; lanes past the row's L lines stay unused), and the rows of the
+// next edges are staged in a per-warp ring in shared memory by cp.async, so that
+// a warp keeps several rows in flight without holding them in registers.
 //
 // A sparse superstep runs in push form instead: a task pass cuts the senders'
 // out-edge lists into tasks of kPushChunk edges, and a warp per task sends
@@ -55,7 +56,7 @@
 // different sources go through their dense supersteps (where nearly every edge
 // carries a message) at about the same superstep, so one pass over the in-edges
 // serves most lanes of every line.  Queries whose source has no out-edges end
-// after superstep 0 and are written directly, without a lane; V is the smallest
+// after superstep 0 and are written directly, without a lane; L is the smallest
 // line count that holds the others (within free device memory).
 //
 // The superstep loop runs on the device: a CUDA graph holds a conditional WHILE
@@ -137,10 +138,9 @@ __device__ __forceinline__ uint32_t* fr_next(uint32_t* fr0, uint32_t* fr1, const
     return ctl->cur ? fr0 : fr1;
 }
 
-// index of lane `lane` of line j of vertex v in the [n][V][32] value arrays
-template <int V>
-__device__ __forceinline__ uint64_t slot_at(uint32_t v, uint32_t j, uint32_t lane) {
-    return ((uint64_t)v * V + j) * kLanes + lane;
+// index of lane `lane` of line j of vertex v in the [n][L][32] value arrays (rows of L lines)
+__device__ __forceinline__ uint64_t slot_at(uint32_t v, uint32_t j, uint32_t lane, uint32_t L) {
+    return ((uint64_t)v * L + j) * kLanes + lane;
 }
 
 __global__ void chunk_rows_kernel(const uint64_t* __restrict__ off, uint32_t n, uint64_t m, uint64_t chunks,
@@ -180,10 +180,10 @@ __device__ __forceinline__ bool batch_push_pick(unsigned long long edges, unsign
 // Lanes `mask` of line j of v were lowered: mark them; the first mark of the
 // vertex (over all its lines) appends it to the next frontier.
 template <int V>
-__device__ __forceinline__ void mark_lowered(uint32_t v, uint32_t j, uint32_t mask, uint32_t* __restrict__ cmask,
-                                             uint32_t* __restrict__ cany, uint32_t* __restrict__ next,
-                                             BatchCounters* __restrict__ ctr) {
-    if (atomicOr(&cmask[(uint64_t)v * V + j], mask) != 0) return;
+__device__ __forceinline__ void mark_lowered(uint32_t v, uint32_t j, uint32_t L, uint32_t mask,
+                                             uint32_t* __restrict__ cmask, uint32_t* __restrict__ cany,
+                                             uint32_t* __restrict__ next, BatchCounters* __restrict__ ctr) {
+    if (atomicOr(&cmask[(uint64_t)v * L + j], mask) != 0) return;
     if (V > 1 && atomicOr(&cany[v], 1u << j) != 0) return;
     next[atomicAdd(&ctr->next_size, 1u)] = v;
 }
@@ -196,14 +196,14 @@ __device__ __forceinline__ void mark_lowered(uint32_t v, uint32_t j, uint32_t ma
 template <int V>
 __global__ void batch_refill_kernel(BatchCtl* __restrict__ ctl, const uint32_t* __restrict__ inv,
                                     const uint64_t* __restrict__ off, const uint32_t* __restrict__ wmax_out,
-                                    uint64_t m, uint32_t* __restrict__ dist,
+                                    uint64_t m, uint32_t L, uint32_t* __restrict__ dist,
                                     uint32_t* __restrict__ sval, uint32_t* __restrict__ smask,
                                     uint32_t* __restrict__ sany, uint32_t* fr0, uint32_t* fr1) {
     __shared__ uint32_t free_sh[V], take_sh[V];
     __shared__ unsigned long long add_sh[V];
     const uint32_t b = threadIdx.x, j = b / kLanes, t = b % kLanes;
     const uint32_t live = ctl->live[j];
-    const bool is_free = !(((live | ctl->pending[j]) >> t) & 1u);
+    const bool is_free = j < L && !(((live | ctl->pending[j]) >> t) & 1u);  // lines past L are not in the rows
     const unsigned freem = __ballot_sync(0xFFFFFFFFu, is_free);
     if (t == 0) free_sh[j] = __popc(freem);
     __syncthreads();
@@ -230,12 +230,12 @@ __global__ void batch_refill_kernel(BatchCtl* __restrict__ ctl, const uint32_t* 
     unsigned long long add = 0;
     if (take) {
         const uint32_t v = inv[src];
-        const uint64_t at = slot_at<V>(v, j, t);
+        const uint64_t at = slot_at(v, j, t, L);
         dist[at] = 0;
         sval[at] = 0;
         const uint64_t deg = off[v + 1] - off[v];
         if (wmax_out[v] == kInf) atomicOr(&ctl->status, kStatusOverflow);  // 0 + w reaches kInf
-        if (atomicOr(&smask[(uint64_t)v * V + j], 1u << t) == 0) {
+        if (atomicOr(&smask[(uint64_t)v * L + j], 1u << t) == 0) {
             add = deg;  // a line of v starts sending
             if (V == 1 || atomicOr(&sany[v], 1u << j) == 0) fr_cur(fr0, fr1, ctl)[atomicAdd(&ctl->f, 1u)] = v;
         }
@@ -314,22 +314,23 @@ struct Flush {
     uint32_t v = 0, pend = 0;  // destination and its lines (pend == 0: nothing outstanding)
     uint32_t r[V], old[V];     // lane's minimum and the value its atomicMin found, per line
 
-    __device__ __forceinline__ void finish(uint32_t lane, uint32_t* __restrict__ cmask, uint32_t* __restrict__ cany,
-                                           uint32_t* __restrict__ next, BatchCounters* __restrict__ ctr) {
+    __device__ __forceinline__ void finish(uint32_t lane, uint32_t L, uint32_t* __restrict__ cmask,
+                                           uint32_t* __restrict__ cany, uint32_t* __restrict__ next,
+                                           BatchCounters* __restrict__ ctr) {
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             if (!((pend >> j) & 1u)) continue;
             const unsigned mask = __ballot_sync(0xFFFFFFFFu, r[j] < old[j]);
-            if (mask && lane == 0) mark_lowered<V>(v, (uint32_t)j, mask, cmask, cany, next, ctr);
+            if (mask && lane == 0) mark_lowered<V>(v, (uint32_t)j, L, mask, cmask, cany, next, ctr);
         }
         pend = 0;
     }
 
     __device__ __forceinline__ void issue(uint32_t dst, const uint32_t (&run)[V], uint32_t lines, uint32_t lane,
-                                          uint32_t* __restrict__ sh, uint32_t* __restrict__ dist,
+                                          uint32_t L, uint32_t* __restrict__ sh, uint32_t* __restrict__ dist,
                                           uint32_t* __restrict__ cmask, uint32_t* __restrict__ cany,
                                           uint32_t* __restrict__ next, BatchCounters* __restrict__ ctr) {
-        finish(lane, cmask, cany, next, ctr);
+        finish(lane, L, cmask, cany, next, ctr);
         if (V == 1) {
             r[0] = run[0];
         } else {
@@ -349,7 +350,7 @@ struct Flush {
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             old[j] = kInf;
-            if (((lines >> j) & 1u) && r[j] != kInf) old[j] = atomicMin(&dist[slot_at<V>(dst, j, lane)], r[j]);
+            if (((lines >> j) & 1u) && r[j] != kInf) old[j] = atomicMin(&dist[slot_at(dst, j, lane, L)], r[j]);
         }
         v = dst;
         pend = lines;
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
                     if (!one_row) {
                         const uint32_t e = j0 + (uint32_t)jj[q];
                         if (e >= bound) {  // the destination changed (warp-uniform)
-                            if (pend) fl.issue(row, run, pend, lane, nullptr, dist, cmask, nullptr, next, ctr);
+                            if (pend) fl.issue(row, run, pend, lane, 1u, nullptr, dist, cmask, nullptr, next, ctr);
                             run[0] = kInf;
                             pend = 0;
                             win.seek(csc_off, n, e_begin, e, lane, row, bound);
@@ -482,8 +483,8 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
             u_l = u_1, w_l = w_1, a_l = a_1;
             u_1 = u_2, w_1 = w_2;
         }
-        if (pend) fl.issue(row, run, pend, lane, nullptr, dist, cmask, nullptr, next, ctr);
-        fl.finish(lane, cmask, nullptr, next, ctr);
+        if (pend) fl.issue(row, run, pend, lane, 1u, nullptr, dist, cmask, nullptr, next, ctr);
+        fl.finish(lane, 1u, cmask, nullptr, next, ctr);
     }
 }
 
@@ -503,30 +504,36 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // Pull form of a superstep with more than one line.  As batch_pull_kernel, but
-// the source rows of the active edges are staged in a per-warp ring of kSlots
-// rows in shared memory: each thread copies its own vectors of an edge's row
-// (the lines that hold a sender) with cp.async and folds them kSlots edges
-// later, so that a warp has kSlots rows in flight without holding them in
-// registers.  A thread reads back only what it copied itself.
+// the source rows of the active edges are staged in a per-warp ring of
+// kRingSlots rows in shared memory: each thread copies its own vectors of an
+// edge's row (the lines that hold a sender) with cp.async and folds them
+// kRingSlots edges later, so that a warp has that many rows in flight without
+// holding them in registers.  A thread reads back only what it copied itself.
+// Dynamic shared memory: ring_smem_bytes(V, L).
+constexpr int kRingWarps = 4;   // warps per block
+constexpr int kRingSlots = 16;  // rows in flight per warp
+
+__host__ __device__ constexpr size_t ring_smem_bytes(int V, uint32_t L) {
+    return sizeof(uint32_t) * kRingWarps * ((size_t)V * kLanes + (size_t)kRingSlots * L * kLanes);
+}
+
 template <int kWeightKind, int V>
-__global__ void __launch_bounds__(128, 5) batch_pull_ring_kernel(
+__global__ void __launch_bounds__(kRingWarps * 32) batch_pull_ring_kernel(
     const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ csc_src, const uint8_t* __restrict__ w8,
     const uint32_t* __restrict__ w32, const uint32_t* __restrict__ chunk_row, uint64_t chunks, uint32_t n,
-    uint64_t m, const uint32_t* __restrict__ sval, const uint32_t* __restrict__ sany, uint32_t* __restrict__ dist,
-    uint32_t* __restrict__ cmask, uint32_t* __restrict__ cany, uint32_t* fr0, uint32_t* fr1,
-    const BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t chunk) {
+    uint64_t m, uint32_t L, const uint32_t* __restrict__ sval, const uint32_t* __restrict__ sany,
+    uint32_t* __restrict__ dist, uint32_t* __restrict__ cmask, uint32_t* __restrict__ cany, uint32_t* fr0,
+    uint32_t* fr1, const BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t chunk) {
     using W = Wide<V>;
-    constexpr int kWarps = 4;
-    constexpr int kSlots = 8;             // rows in flight per warp
-    constexpr uint32_t kRow = V * kLanes;  // words per row
-    __shared__ __align__(16) uint32_t ring_sh[kWarps * kSlots * kRow];
-    __shared__ __align__(16) uint32_t flush_sh[kWarps * kRow];
+    constexpr int kSlots = kRingSlots;
+    extern __shared__ __align__(16) uint32_t ring_dyn[];
     if (ctl->push) return;
+    const uint32_t kRow = L * kLanes;  // words per row
     uint32_t* __restrict__ next = fr_next(fr0, fr1, ctl);
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const uint32_t* ring = ring_sh + wib * kSlots * kRow;
+    uint32_t* __restrict__ sh = ring_dyn + wib * (V * kLanes);  // flush buffers first
+    const uint32_t* ring = ring_dyn + kRingWarps * (V * kLanes) + wib * kSlots * kRow;
     const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
-    uint32_t* __restrict__ sh = flush_sh + wib * kRow;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t my_line[W::kVec];
@@ -553,7 +560,7 @@ __global__ void __launch_bounds__(128, 5) batch_pull_ring_kernel(
             const uint32_t w = __shfl_sync(0xFFFFFFFFu, m_w, slot);
             const uint32_t a = __shfl_sync(0xFFFFFFFFu, m_a, slot);
             if (e >= bound) {  // the destination changed (warp-uniform)
-                if (pend) fl.issue(row, run, pend, lane, sh, dist, cmask, cany, next, ctr);
+                if (pend) fl.issue(row, run, pend, lane, L, sh, dist, cmask, cany, next, ctr);
 #pragma unroll
                 for (int j = 0; j < V; ++j) run[j] = kInf;
                 pend = 0;
@@ -615,8 +622,8 @@ __global__ void __launch_bounds__(128, 5) batch_pull_ring_kernel(
         }
         cp_async_wait<0>();
         while (folded < issued) fold_one();
-        if (pend) fl.issue(row, run, pend, lane, sh, dist, cmask, cany, next, ctr);
-        fl.finish(lane, cmask, cany, next, ctr);
+        if (pend) fl.issue(row, run, pend, lane, L, sh, dist, cmask, cany, next, ctr);
+        fl.finish(lane, L, cmask, cany, next, ctr);
     }
 }
 
@@ -672,7 +679,7 @@ constexpr int kSparseLanes = 4;
 template <int kWeightKind, int V>
 __global__ void __launch_bounds__(256) batch_push_kernel(
     const uint64_t* __restrict__ off, const uint32_t* __restrict__ col, const uint8_t* __restrict__ w8,
-    const uint32_t* __restrict__ w32, const unsigned long long* __restrict__ tasks,
+    const uint32_t* __restrict__ w32, const unsigned long long* __restrict__ tasks, uint32_t L,
     const uint32_t* __restrict__ sval, const uint32_t* __restrict__ smask, const uint32_t* __restrict__ sany,
     uint32_t* __restrict__ dist, uint32_t* __restrict__ cmask, uint32_t* __restrict__ cany, uint32_t* fr0,
     uint32_t* fr1, const BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr) {
@@ -692,7 +699,7 @@ __global__ void __launch_bounds__(256) batch_push_kernel(
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             if (!((lines >> j) & 1u)) continue;
-            const uint32_t senders = smask[(uint64_t)u * V + j];  // sending lanes of line j (warp-uniform)
+            const uint32_t senders = smask[(uint64_t)u * L + j];  // sending lanes of line j (warp-uniform)
             if (__popc(senders) > kSparseLanes) {
                 dense |= 1u << j;
                 continue;
@@ -705,11 +712,11 @@ __global__ void __launch_bounds__(256) batch_push_kernel(
                 if (kWeightKind == 2) w = __ldg(w32 + e);
                 for (uint32_t rest = senders; rest; rest &= rest - 1) {
                     const uint32_t b = __ffs(rest) - 1;
-                    const uint32_t s = __ldg(sval + slot_at<V>(u, j, b));
+                    const uint32_t s = __ldg(sval + slot_at(u, j, b, L));
                     if (s != kInf) {
                         const uint32_t d = batch_cand(s, w, ctr);
-                        if (d < atomicMin(&dist[slot_at<V>(v, j, b)], d))
-                            mark_lowered<V>(v, (uint32_t)j, 1u << b, cmask, cany, next, ctr);
+                        if (d < atomicMin(&dist[slot_at(v, j, b, L)], d))
+                            mark_lowered<V>(v, (uint32_t)j, L, 1u << b, cmask, cany, next, ctr);
                     }
                 }
             }
@@ -718,7 +725,7 @@ __global__ void __launch_bounds__(256) batch_push_kernel(
         // kInf: the lane does not send from u in that line
         uint32_t s[V];
 #pragma unroll
-        for (int j = 0; j < V; ++j) s[j] = (dense >> j) & 1u ? sval[slot_at<V>(u, j, lane)] : kInf;
+        for (int j = 0; j < V; ++j) s[j] = (dense >> j) & 1u ? sval[slot_at(u, j, lane, L)] : kInf;
         for (uint64_t j0 = e_beg; j0 < e_end; j0 += 32) {
             const uint32_t cnt = (uint32_t)min((uint64_t)32, e_end - j0);
             uint32_t v_l = 0, w_l = 1;
@@ -736,10 +743,10 @@ __global__ void __launch_bounds__(256) batch_push_kernel(
                     bool changed = false;
                     if (s[j] != kInf) {
                         const uint32_t d = batch_cand(s[j], w, ctr);
-                        changed = d < atomicMin(&dist[slot_at<V>(v, j, lane)], d);
+                        changed = d < atomicMin(&dist[slot_at(v, j, lane, L)], d);
                     }
                     const unsigned mask = __ballot_sync(0xFFFFFFFFu, changed);
-                    if (mask && lane == 0) mark_lowered<V>(v, (uint32_t)j, mask, cmask, cany, next, ctr);
+                    if (mask && lane == 0) mark_lowered<V>(v, (uint32_t)j, L, mask, cmask, cany, next, ctr);
                 }
             }
         }
@@ -748,7 +755,7 @@ __global__ void __launch_bounds__(256) batch_push_kernel(
 
 // previous senders: snapshot rows back to kInf, sender masks cleared
 template <int V>
-__global__ void batch_reset_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl,
+__global__ void batch_reset_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl, uint32_t L,
                                    uint32_t* __restrict__ sval, uint32_t* __restrict__ smask,
                                    uint32_t* __restrict__ sany) {
     using W = Wide<V>;
@@ -768,11 +775,11 @@ __global__ void batch_reset_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl*
             continue;
         }
         const uint32_t lines = sany[u];
-        uint32_t* rowp = sval + (uint64_t)u * (V * kLanes);
+        uint32_t* rowp = sval + (uint64_t)u * (L * kLanes);
 #pragma unroll
         for (int k = 0; k < W::kVec; ++k)
             if ((lines >> W::line(lane, k)) & 1u) wide_store<V>(rowp, lane, k, inf);
-        if (lane < (uint32_t)V && ((lines >> lane) & 1u)) smask[(uint64_t)u * V + lane] = 0;
+        if (lane < L && ((lines >> lane) & 1u)) smask[(uint64_t)u * L + lane] = 0;
         __syncwarp();
         if (lane == 0) sany[u] = 0;
     }
@@ -783,7 +790,7 @@ __global__ void batch_reset_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl*
 // would reach kInf (x + the largest out-edge weight of the vertex >= kInf).
 template <int V>
 __global__ void batch_apply_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl* __restrict__ ctl, uint32_t n,
-                                   const uint64_t* __restrict__ off, const uint32_t* __restrict__ wmax_out,
+                                   uint32_t L, const uint64_t* __restrict__ off, const uint32_t* __restrict__ wmax_out,
                                    const uint32_t* __restrict__ dist, uint32_t* __restrict__ sval,
                                    uint32_t* __restrict__ smask, uint32_t* __restrict__ sany,
                                    uint32_t* __restrict__ cmask, uint32_t* __restrict__ cany,
@@ -824,13 +831,13 @@ __global__ void batch_apply_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl*
             const uint32_t lines = cany[v];
             const uint64_t deg = off[v + 1] - off[v];
             const uint32_t lim = kInf - wmax_out[v];  // a sent value must stay below this
-            const uint64_t rowi = (uint64_t)v * (V * kLanes);
+            const uint64_t rowi = (uint64_t)v * (L * kLanes);
 #pragma unroll
             for (int k = 0; k < W::kVec; ++k) {
                 const uint32_t j = W::line(lane, k);
                 if (!((lines >> j) & 1u)) continue;
                 const uint32_t mine =
-                    (cmask[(uint64_t)v * V + j] >> (W::lane0(lane, k) % kLanes)) & ((1u << W::kW) - 1u);
+                    (cmask[(uint64_t)v * L + j] >> (W::lane0(lane, k) % kLanes)) & ((1u << W::kW) - 1u);
                 if (!mine) continue;
                 uint32_t x[W::kW];
                 wide_load<V>(dist + rowi, lane, k, true, x);
@@ -847,8 +854,8 @@ __global__ void batch_apply_kernel(uint32_t* fr0, uint32_t* fr1, const BatchCtl*
             }
             edges += deg * (uint64_t)__popc(lines);
             __syncwarp();  // every thread has read the lowered-lane masks
-            if (lane < (uint32_t)V && ((lines >> lane) & 1u)) {
-                const uint64_t wi = (uint64_t)v * V + lane;
+            if (lane < L && ((lines >> lane) & 1u)) {
+                const uint64_t wi = (uint64_t)v * L + lane;
                 smask[wi] = cmask[wi];
                 cmask[wi] = 0;
             }
@@ -984,7 +991,7 @@ __global__ void batch_step_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __r
 // warp's writes of one lane cover 32 consecutive words of its output row.
 template <int V>
 __global__ void batch_harvest_kernel(const BatchCtl* __restrict__ ctl, const uint32_t* __restrict__ inv, uint32_t n,
-                                     uint32_t* __restrict__ dist) {
+                                     uint32_t L, uint32_t* __restrict__ dist) {
     __shared__ uint32_t fin_sh[V];
     __shared__ uint32_t row_sh[V * kLanes];
     uint32_t any = 0;
@@ -998,7 +1005,7 @@ __global__ void batch_harvest_kernel(const BatchCtl* __restrict__ ctl, const uin
     const uint64_t stride = ctl->out_stride;
     const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += step) {
-        uint32_t* d = dist + (uint64_t)inv[v] * (V * kLanes);
+        uint32_t* d = dist + (uint64_t)inv[v] * (L * kLanes);
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             for (uint32_t r = fin_sh[j]; r; r &= r - 1) {
@@ -1017,17 +1024,19 @@ unsigned grid_for_warps(uint64_t warps, int sms) {
     return (unsigned)(blocks < cap ? blocks : cap);
 }
 
-int lines_index(uint32_t lines) { return lines >= 8 ? 3 : lines >= 4 ? 2 : lines >= 2 ? 1 : 0; }
+// lanes per thread of the wide kernels for rows of L lines: the next of 1, 2, 4, 8
+int lines_v(uint32_t L) { return L > 4 ? 8 : L > 2 ? 4 : L > 1 ? 2 : 1; }
 
 }  // namespace
 
 // Batch workspace lives with the graph; allocated on first use.
 struct BatchWorkspace {
-    uint32_t lines = 0;         // lines per vertex the value arrays hold (0: not allocated yet)
-    uint32_t* dist = nullptr;   // [n][lines][32]
-    uint32_t* sval = nullptr;   // [n][lines][32]
-    uint32_t* smask = nullptr;  // [n][lines]
-    uint32_t* cmask = nullptr;  // [n][lines]
+    uint32_t lines = 0;         // lines per vertex the value arrays hold (0: not allocated yet);
+                                // a session with L <= lines lines lays its rows out [n][L][32]
+    uint32_t* dist = nullptr;   // [n][L][32]
+    uint32_t* sval = nullptr;   // [n][L][32]
+    uint32_t* smask = nullptr;  // [n][L]
+    uint32_t* cmask = nullptr;  // [n][L]
     uint32_t* sany = nullptr;   // [n]: lines with a sender (used with more than one line)
     uint32_t* cany = nullptr;   // [n]: lines with a lowered lane
     uint32_t* fr[2] = {nullptr, nullptr};
@@ -1047,7 +1056,7 @@ struct BatchWorkspace {
     unsigned long long* tasks = nullptr;  // push tasks of the current senders
     bool clean = false;                   // dist/sval all kInf, masks and counters zero
     ipg_batch_info info{};                // totals of the last ipg_sssp_batch call
-    cudaGraphExec_t loop[3][4] = {};      // superstep loop, per weight kind and line count
+    cudaGraphExec_t loop[3][kMaxLines] = {};  // superstep loop, per weight kind and line count
 };
 
 static void batch_drop_loops(BatchWorkspace* b) {
@@ -1143,16 +1152,16 @@ static ipg_status batch_values(ipg_graph* g, BatchWorkspace* b, uint32_t lines) 
 }
 
 // Lines for a session whose `sending` queries should all start at once: the
-// fewest lines (a power of two, at most kMaxLines) that hold them, fewer if the
-// value arrays would not fit in three quarters of free device memory.
+// fewest lines (at most kMaxLines) that hold them, fewer if the value arrays
+// would not fit in three quarters of free device memory.
 static uint32_t batch_lines_for(const ipg_graph* g, const BatchWorkspace* b, uint64_t sending) {
-    uint32_t want = 1;
-    while (want < (uint32_t)kMaxLines && (uint64_t)want * kLanes < sending) want <<= 1;
+    uint32_t want = (uint32_t)((sending + kLanes - 1) / kLanes);
+    want = want < 1 ? 1 : want > (uint32_t)kMaxLines ? (uint32_t)kMaxLines : want;
     if (b->lines >= want) return want;
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return b->lines ? b->lines : 1;
     const size_t held = b->lines ? batch_value_bytes(g->n, b->lines) : 0;  // freed before the new arrays
-    while (want > 1 && batch_value_bytes(g->n, want) > (fr + held) / 4 * 3) want >>= 1;
+    while (want > 1 && batch_value_bytes(g->n, want) > (fr + held) / 4 * 3) --want;
     return want > b->lines ? want : (b->lines ? b->lines : 1);
 }
 
@@ -1184,8 +1193,8 @@ static ipg_status batch_chunks(ipg_graph* g, BatchWorkspace* b, cudaStream_t st)
 // the superstep body for V lines, enqueued on `st` (captured into the loop graph,
 // or launched directly when in_graph is 0)
 template <int V>
-static void batch_superstep_lines(ipg_graph* g, BatchWorkspace* b, int wkind, cudaGraphConditionalHandle loop,
-                                  int in_graph, cudaStream_t st) {
+static void batch_superstep_lines(ipg_graph* g, BatchWorkspace* b, int wkind, uint32_t L,
+                                  cudaGraphConditionalHandle loop, int in_graph, cudaStream_t st) {
     const int sms = sm_count_of(g->device);
     const unsigned grid = grid_for_warps(b->chunks, sms);
     const unsigned fixed = (unsigned)sms * 8;  // frontier passes: persistent, the size is read on the device
@@ -1195,16 +1204,15 @@ static void batch_superstep_lines(ipg_graph* g, BatchWorkspace* b, int wkind, cu
                                                    b->chunks, g->n, g->m, b->sval, b->smask, b->dist, b->cmask,     \
                                                    b->fr[0], b->fr[1], b->ctl, b->ctr, b->chunk);                   \
     else                                                                                                            \
-        batch_pull_ring_kernel<K, V><<<2 * grid, 128, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w,        \
-                                                               b->chunk_row, b->chunks, g->n, g->m, b->sval, b->sany,\
-                                                               b->dist, b->cmask, b->cany, b->fr[0], b->fr[1],      \
-                                                               b->ctl, b->ctr, b->chunk)
+        batch_pull_ring_kernel<K, V><<<2 * grid, kRingWarps * 32, ring_smem_bytes(V, L), st>>>(                    \
+            g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row, b->chunks, g->n, g->m, L, b->sval, b->sany,  \
+            b->dist, b->cmask, b->cany, b->fr[0], b->fr[1], b->ctl, b->ctr, b->chunk)
 #define IPG_BATCH_PUSH(K)                                                                                           \
-    batch_push_kernel<K, V><<<fixed, 256, 0, st>>>(g->off, g->col, g->w8, g->w, b->tasks, b->sval, b->smask,      \
+    batch_push_kernel<K, V><<<fixed, 256, 0, st>>>(g->off, g->col, g->w8, g->w, b->tasks, L, b->sval, b->smask,   \
                                                    b->sany, b->dist, b->cmask, b->cany, b->fr[0], b->fr[1], b->ctl, \
                                                    b->ctr)
-    batch_refill_kernel<V><<<1, V * kLanes, 0, st>>>(b->ctl, g->inv, g->off, b->wmax_out, g->m, b->dist, b->sval,
-                                                     b->smask, b->sany, b->fr[0], b->fr[1]);
+    batch_refill_kernel<V><<<1, V * kLanes, 0, st>>>(b->ctl, g->inv, g->off, b->wmax_out, g->m, L, b->dist,
+                                                     b->sval, b->smask, b->sany, b->fr[0], b->fr[1]);
     batch_tasks_kernel<<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, g->off, b->tasks, b->ctr);
     if (wkind == 1) {
         IPG_BATCH_PULL(1);
@@ -1218,27 +1226,52 @@ static void batch_superstep_lines(ipg_graph* g, BatchWorkspace* b, int wkind, cu
     }
 #undef IPG_BATCH_PULL
 #undef IPG_BATCH_PUSH
-    batch_reset_kernel<V><<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, b->sval, b->smask, b->sany);
-    batch_apply_kernel<V><<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, g->n, g->off, b->wmax_out, b->dist,
-                                                 b->sval, b->smask, b->sany, b->cmask, b->cany, b->ctr);
+    batch_reset_kernel<V><<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, L, b->sval, b->smask, b->sany);
+    batch_apply_kernel<V><<<fixed, 256, 0, st>>>(b->fr[0], b->fr[1], b->ctl, g->n, L, g->off, b->wmax_out,
+                                                 b->dist, b->sval, b->smask, b->sany, b->cmask, b->cany, b->ctr);
     batch_step_kernel<V><<<1, V * kLanes, 0, st>>>(b->ctl, b->ctr, g->n, loop, in_graph);
-    batch_harvest_kernel<V><<<fixed, 256, 0, st>>>(b->ctl, g->inv, g->n, b->dist);
+    batch_harvest_kernel<V><<<fixed, 256, 0, st>>>(b->ctl, g->inv, g->n, L, b->dist);
 }
 
 static void batch_superstep(ipg_graph* g, BatchWorkspace* b, int wkind, uint32_t lines,
                             cudaGraphConditionalHandle loop, int in_graph, cudaStream_t st) {
-    switch (lines_index(lines)) {
-        case 3: batch_superstep_lines<8>(g, b, wkind, loop, in_graph, st); break;
-        case 2: batch_superstep_lines<4>(g, b, wkind, loop, in_graph, st); break;
-        case 1: batch_superstep_lines<2>(g, b, wkind, loop, in_graph, st); break;
-        default: batch_superstep_lines<1>(g, b, wkind, loop, in_graph, st); break;
+    switch (lines_v(lines)) {
+        case 8: batch_superstep_lines<8>(g, b, wkind, lines, loop, in_graph, st); break;
+        case 4: batch_superstep_lines<4>(g, b, wkind, lines, loop, in_graph, st); break;
+        case 2: batch_superstep_lines<2>(g, b, wkind, lines, loop, in_graph, st); break;
+        default: batch_superstep_lines<1>(g, b, wkind, lines, loop, in_graph, st); break;
     }
+}
+
+// the wide pull's dynamic shared memory for rows of L lines (above the default 48 KB
+// limit for 8 lines); set before the kernel is launched or captured
+template <int V>
+static cudaError_t ring_smem_allow(uint32_t L) {
+    const int bytes = (int)ring_smem_bytes(V, L);
+    cudaError_t e = cudaFuncSetAttribute(batch_pull_ring_kernel<0, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_pull_ring_kernel<1, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_pull_ring_kernel<2, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+static ipg_status batch_ring_allow(uint32_t lines) {
+    cudaError_t e = cudaSuccess;
+    switch (lines_v(lines)) {
+        case 8: e = ring_smem_allow<8>(lines); break;
+        case 4: e = ring_smem_allow<4>(lines); break;
+        case 2: e = ring_smem_allow<2>(lines); break;
+        default: break;
+    }
+    return e == cudaSuccess ? IPG_OK : cuda_fail(e, "batched pull shared memory", __FILE__, __LINE__);
 }
 
 // Builds the graph [WHILE (cond) { superstep }] for this workspace, weight kind and line count.
 static ipg_status batch_loop_graph(ipg_graph* g, BatchWorkspace* b, int wkind, uint32_t lines) {
-    cudaGraphExec_t& exec = b->loop[wkind][lines_index(lines)];
+    cudaGraphExec_t& exec = b->loop[wkind][lines - 1];
     if (exec) return IPG_OK;
+    IPG_TRY(batch_ring_allow(lines));
     cudaGraph_t graph = nullptr;
     cudaStream_t cap = nullptr;
     ipg_status rc = IPG_OK;
@@ -1309,11 +1342,12 @@ static BatchCtl batch_ctl_init(const ipg_graph* g, uint32_t lines) {
 static ipg_status batch_launch(ipg_graph* g, BatchWorkspace* b, cudaStream_t st, const char* name) {
     if (tuning().batch_loop) {
         IPG_TRY(batch_loop_graph(g, b, weight_kind(g), b->h_ctl->lines));
-        IPG_CUDA(cudaGraphLaunch(b->loop[weight_kind(g)][lines_index(b->h_ctl->lines)], st));
+        IPG_CUDA(cudaGraphLaunch(b->loop[weight_kind(g)][b->h_ctl->lines - 1], st));
         IPG_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
         IPG_CUDA(cudaStreamSynchronize(st));
     } else {
         // the step kernel leaves iter at 0 where the graph's WHILE condition would end
+        IPG_TRY(batch_ring_allow(b->h_ctl->lines));
         for (;;) {
             batch_superstep(g, b, weight_kind(g), b->h_ctl->lines, cudaGraphConditionalHandle{}, 0, st);
             IPG_CUDA(cudaGetLastError());
