@@ -505,40 +505,67 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Pull form of a superstep with more than one line.  As batch_pull_kernel, but
 // the source rows of the active edges are staged in a per-warp ring of
-// kRingSlots rows in shared memory: each thread copies its own vectors of an
-// edge's row (the lines that hold a sender) with cp.async and folds them
+// kRingSlots rows in shared memory: each thread copies its own words of an
+// edge's row (in the lines that hold a sender) with cp.async and folds them
 // kRingSlots edges later, so that a warp has that many rows in flight without
-// holding them in registers.  A thread reads back only what it copied itself.
-// Dynamic shared memory: ring_smem_bytes(V, L).
+// holding them in registers.  A thread reads back only what it copied itself;
+// the edge's position, weight and sender lines go through a per-warp slot in
+// shared memory.
+//
+// A row of L lines maps to the warp's threads as RowMap<L> says: 16-byte
+// vectors for the first 4 (L / 4) lines, then one word per thread for each of
+// the L % 4 lines left, so every thread folds exactly L words.
+// Dynamic shared memory: ring_smem_bytes(L).
 constexpr int kRingWarps = 4;   // warps per block
 constexpr int kRingSlots = 16;  // rows in flight per warp
 
-__host__ __device__ constexpr size_t ring_smem_bytes(int V, uint32_t L) {
-    return sizeof(uint32_t) * kRingWarps * ((size_t)V * kLanes + (size_t)kRingSlots * L * kLanes);
+__host__ __device__ constexpr size_t ring_smem_bytes(uint32_t L) {
+    return sizeof(uint32_t) * kRingWarps * ((size_t)L * kLanes + (size_t)kRingSlots * L * kLanes) +
+           sizeof(uint4) * kRingWarps * kRingSlots;
 }
 
-template <int kWeightKind, int V>
+template <int L>
+struct RowMap {
+    static constexpr int kVec = L / 4;               // vectors: lanes 128 k + 4 t .. + 3 (line 4 k + t / 8)
+    static constexpr int kScal = L % 4;              // words: lane 32 (4 kVec + i) + t (line 4 kVec + i)
+    static constexpr int kWords = 4 * kVec + kScal;  // = L
+    __device__ __forceinline__ static uint32_t vec_off(uint32_t t, int k) { return 128u * k + 4u * t; }
+    __device__ __forceinline__ static uint32_t vec_line(uint32_t t, int k) { return 4u * k + t / 8u; }
+    __device__ __forceinline__ static uint32_t scal_off(uint32_t t, int i) { return 32u * (4 * kVec + i) + t; }
+    static constexpr uint32_t scal_line(int i) { return 4u * kVec + i; }
+};
+
+// run = min(run, s + w) for a sender value s, run unchanged for s = kInf (as
+// batch_fold), with the fused add-min
+__device__ __forceinline__ void batch_fold2(uint32_t& run, uint32_t s, uint32_t w, uint32_t lim) {
+    run = __viaddmin_u32(min(s, lim), w, run);
+}
+
+template <int kWeightKind, int L>
 __global__ void __launch_bounds__(kRingWarps * 32) batch_pull_ring_kernel(
     const uint64_t* __restrict__ csc_off, const uint32_t* __restrict__ csc_src, const uint8_t* __restrict__ w8,
     const uint32_t* __restrict__ w32, const uint32_t* __restrict__ chunk_row, uint64_t chunks, uint32_t n,
-    uint64_t m, uint32_t L, const uint32_t* __restrict__ sval, const uint32_t* __restrict__ sany,
+    uint64_t m, const uint32_t* __restrict__ sval, const uint32_t* __restrict__ sany,
     uint32_t* __restrict__ dist, uint32_t* __restrict__ cmask, uint32_t* __restrict__ cany, uint32_t* fr0,
     uint32_t* fr1, const BatchCtl* __restrict__ ctl, BatchCounters* __restrict__ ctr, uint32_t chunk) {
-    using W = Wide<V>;
+    using M = RowMap<L>;
     constexpr int kSlots = kRingSlots;
+    constexpr uint32_t kRow = L * kLanes;  // words per row
     extern __shared__ __align__(16) uint32_t ring_dyn[];
     if (ctl->push) return;
-    const uint32_t kRow = L * kLanes;  // words per row
     uint32_t* __restrict__ next = fr_next(fr0, fr1, ctl);
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t* __restrict__ sh = ring_dyn + wib * (V * kLanes);  // flush buffers first
-    const uint32_t* ring = ring_dyn + kRingWarps * (V * kLanes) + wib * kSlots * kRow;
+    uint4* meta = reinterpret_cast<uint4*>(ring_dyn) + wib * kSlots;  // per slot: edge, weight, lines
+    uint32_t* __restrict__ sh = ring_dyn + (kRingWarps * kSlots * 4) + wib * kRow;  // flush buffer
+    const uint32_t* ring = ring_dyn + (kRingWarps * kSlots * 4) + kRingWarps * kRow + wib * kSlots * kRow;
     const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    uint32_t my_line[W::kVec];
+    uint32_t vline[M::kVec > 0 ? M::kVec : 1], voff[M::kVec > 0 ? M::kVec : 1], soff[M::kScal > 0 ? M::kScal : 1];
 #pragma unroll
-    for (int k = 0; k < W::kVec; ++k) my_line[k] = W::line(lane, k);
+    for (int k = 0; k < M::kVec; ++k) vline[k] = M::vec_line(lane, k), voff[k] = M::vec_off(lane, k);
+#pragma unroll
+    for (int i = 0; i < M::kScal; ++i) soff[i] = M::scal_off(lane, i);
     for (uint64_t c = warp; c < chunks; c += nwarps) {
         const uint64_t e_begin = c * chunk;
         const uint32_t len = (uint32_t)(e_begin + chunk < m ? chunk : m - e_begin);
@@ -546,42 +573,68 @@ __global__ void __launch_bounds__(kRingWarps * 32) batch_pull_ring_kernel(
         win.load(csc_off, n, chunk_row[c], e_begin, lane);
         uint32_t row = win.base;
         uint32_t bound = __shfl_sync(0xFFFFFFFFu, win.end_l, 0);
-        uint32_t run[V];
+        uint32_t run[L];  // the thread's words: vectors, then single words
 #pragma unroll
-        for (int j = 0; j < V; ++j) run[j] = kInf;
+        for (int j = 0; j < L; ++j) run[j] = kInf;
         uint32_t pend = 0;
-        Flush<V> fl;
-        uint32_t m_e = 0, m_w = 0, m_a = 0;  // lane s < kSlots: edge, weight and lines of ring slot s
+        uint32_t f_v = 0, f_pend = 0, f_r[L], f_old[L];  // the flush in flight: destination, lines, values
+        // the outstanding flush: mark the lanes whose value dropped
+        auto finish = [&]() {
+#pragma unroll
+            for (int j = 0; j < L; ++j) {
+                if (!((f_pend >> j) & 1u)) continue;
+                const unsigned mask = __ballot_sync(0xFFFFFFFFu, f_r[j] < f_old[j]);
+                if (mask && lane == 0) mark_lowered<L>(f_v, (uint32_t)j, L, mask, cmask, cany, next, ctr);
+            }
+            f_pend = 0;
+        };
+        // the current destination's minima: to line order, one coalesced row of atomicMin per line
+        auto flush = [&]() {
+            finish();
+#pragma unroll
+            for (int k = 0; k < M::kVec; ++k)
+                *reinterpret_cast<uint4*>(sh + voff[k]) =
+                    make_uint4(run[4 * k], run[4 * k + 1], run[4 * k + 2], run[4 * k + 3]);
+#pragma unroll
+            for (int i = 0; i < M::kScal; ++i) sh[soff[i]] = run[4 * M::kVec + i];
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < L; ++j) {
+                f_r[j] = sh[j * kLanes + lane];
+                f_old[j] = kInf;
+                if (((pend >> j) & 1u) && f_r[j] != kInf)
+                    f_old[j] = atomicMin(&dist[slot_at(row, j, lane, L)], f_r[j]);
+            }
+            __syncwarp();  // the buffer is free for the next flush
+            f_v = row;
+            f_pend = pend;
+        };
         uint32_t issued = 0, folded = 0;
         // fold the oldest staged edge (its copies have completed)
         auto fold_one = [&]() {
             const uint32_t slot = folded % kSlots;
-            const uint32_t e = __shfl_sync(0xFFFFFFFFu, m_e, slot);
-            const uint32_t w = __shfl_sync(0xFFFFFFFFu, m_w, slot);
-            const uint32_t a = __shfl_sync(0xFFFFFFFFu, m_a, slot);
+            const uint4 md = meta[slot];  // edge, weight, lines
+            const uint32_t e = md.x, w = md.y, a = md.z, lim = kInf - w;
             if (e >= bound) {  // the destination changed (warp-uniform)
-                if (pend) fl.issue(row, run, pend, lane, L, sh, dist, cmask, cany, next, ctr);
+                if (pend) flush();
 #pragma unroll
-                for (int j = 0; j < V; ++j) run[j] = kInf;
+                for (int j = 0; j < L; ++j) run[j] = kInf;
                 pend = 0;
                 win.seek(csc_off, n, e_begin, e, lane, row, bound);
             }
+            const uint32_t* x = ring + slot * kRow;
 #pragma unroll
-            for (int k = 0; k < W::kVec; ++k) {
-                if (!((a >> my_line[k]) & 1u)) continue;
-                const uint32_t* x = ring + slot * kRow + W::lane0(lane, k);
-                if (V == 2) {
-                    const uint2 y = *reinterpret_cast<const uint2*>(x);
-                    batch_fold(run[k * W::kW + 0], y.x, w);
-                    batch_fold(run[k * W::kW + 1], y.y, w);
-                } else {
-                    const uint4 y = *reinterpret_cast<const uint4*>(x);
-                    batch_fold(run[k * W::kW + 0], y.x, w);
-                    batch_fold(run[k * W::kW + 1], y.y, w);
-                    batch_fold(run[k * W::kW + 2], y.z, w);
-                    batch_fold(run[k * W::kW + 3], y.w, w);
-                }
+            for (int k = 0; k < M::kVec; ++k) {
+                if (!((a >> vline[k]) & 1u)) continue;
+                const uint4 y = *reinterpret_cast<const uint4*>(x + voff[k]);
+                batch_fold2(run[4 * k + 0], y.x, w, lim);
+                batch_fold2(run[4 * k + 1], y.y, w, lim);
+                batch_fold2(run[4 * k + 2], y.z, w, lim);
+                batch_fold2(run[4 * k + 3], y.w, w, lim);
             }
+#pragma unroll
+            for (int i = 0; i < M::kScal; ++i)
+                if ((a >> M::scal_line(i)) & 1u) batch_fold2(run[4 * M::kVec + i], x[soff[i]], w, lim);
             pend |= a;
             ++folded;
         };
@@ -597,7 +650,6 @@ __global__ void __launch_bounds__(kRingWarps * 32) batch_pull_ring_kernel(
                 const int jj = __ffs(active) - 1;
                 active &= active - 1;
                 const uint32_t u = __shfl_sync(0xFFFFFFFFu, u_l, jj);
-                const uint32_t w = __shfl_sync(0xFFFFFFFFu, w_l, jj);
                 const uint32_t a = __shfl_sync(0xFFFFFFFFu, a_l, jj);
                 if (issued - folded == (uint32_t)kSlots) {
                     cp_async_wait<kSlots - 1>();
@@ -605,16 +657,16 @@ __global__ void __launch_bounds__(kRingWarps * 32) batch_pull_ring_kernel(
                 }
                 const uint32_t slot = issued % kSlots;
                 const uint32_t* rowp = sval + (uint64_t)u * kRow;
+                const uint32_t dst = ring_s + slot * kRow * 4u;
 #pragma unroll
-                for (int k = 0; k < W::kVec; ++k)
-                    if ((a >> my_line[k]) & 1u)
-                        cp_async<W::kW * 4>(ring_s + (slot * kRow + W::lane0(lane, k)) * 4u, rowp + W::lane0(lane, k));
+                for (int k = 0; k < M::kVec; ++k)
+                    if ((a >> vline[k]) & 1u) cp_async<16>(dst + voff[k] * 4u, rowp + voff[k]);
+#pragma unroll
+                for (int i = 0; i < M::kScal; ++i)
+                    if ((a >> M::scal_line(i)) & 1u) cp_async<4>(dst + soff[i] * 4u, rowp + soff[i]);
                 cp_async_commit();
-                if (lane == slot) {
-                    m_e = j0 + (uint32_t)jj;
-                    m_w = w;
-                    m_a = a;
-                }
+                if (lane == (uint32_t)jj) meta[slot] = make_uint4(j0 + (uint32_t)jj, w_l, a_l, 0u);
+                __syncwarp();
                 ++issued;
             }
             u_l = u_1, w_l = w_1, a_l = a_1;
@@ -622,8 +674,8 @@ __global__ void __launch_bounds__(kRingWarps * 32) batch_pull_ring_kernel(
         }
         cp_async_wait<0>();
         while (folded < issued) fold_one();
-        if (pend) fl.issue(row, run, pend, lane, L, sh, dist, cmask, cany, next, ctr);
-        fl.finish(lane, L, cmask, cany, next, ctr);
+        if (pend) flush();
+        finish();
     }
 }
 
@@ -1190,6 +1242,27 @@ static ipg_status batch_chunks(ipg_graph* g, BatchWorkspace* b, cudaStream_t st)
     return IPG_OK;
 }
 
+// the wide pull for rows of L lines (2 <= L <= 8)
+template <int K, int L>
+static void ring_launch_l(ipg_graph* g, BatchWorkspace* b, unsigned grid, cudaStream_t st) {
+    batch_pull_ring_kernel<K, L><<<grid, kRingWarps * 32, ring_smem_bytes(L), st>>>(
+        g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row, b->chunks, g->n, g->m, b->sval, b->sany, b->dist,
+        b->cmask, b->cany, b->fr[0], b->fr[1], b->ctl, b->ctr, b->chunk);
+}
+
+template <int K>
+static void batch_ring_launch(ipg_graph* g, BatchWorkspace* b, uint32_t L, unsigned grid, cudaStream_t st) {
+    switch (L) {
+        case 2: ring_launch_l<K, 2>(g, b, grid, st); break;
+        case 3: ring_launch_l<K, 3>(g, b, grid, st); break;
+        case 4: ring_launch_l<K, 4>(g, b, grid, st); break;
+        case 5: ring_launch_l<K, 5>(g, b, grid, st); break;
+        case 6: ring_launch_l<K, 6>(g, b, grid, st); break;
+        case 7: ring_launch_l<K, 7>(g, b, grid, st); break;
+        default: ring_launch_l<K, 8>(g, b, grid, st); break;
+    }
+}
+
 // the superstep body for V lines, enqueued on `st` (captured into the loop graph,
 // or launched directly when in_graph is 0)
 template <int V>
@@ -1204,9 +1277,7 @@ static void batch_superstep_lines(ipg_graph* g, BatchWorkspace* b, int wkind, ui
                                                    b->chunks, g->n, g->m, b->sval, b->smask, b->dist, b->cmask,     \
                                                    b->fr[0], b->fr[1], b->ctl, b->ctr, b->chunk);                   \
     else                                                                                                            \
-        batch_pull_ring_kernel<K, V><<<2 * grid, kRingWarps * 32, ring_smem_bytes(V, L), st>>>(                    \
-            g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row, b->chunks, g->n, g->m, L, b->sval, b->sany,  \
-            b->dist, b->cmask, b->cany, b->fr[0], b->fr[1], b->ctl, b->ctr, b->chunk)
+        batch_ring_launch<K>(g, b, L, 2 * grid, st)
 #define IPG_BATCH_PUSH(K)                                                                                           \
     batch_push_kernel<K, V><<<fixed, 256, 0, st>>>(g->off, g->col, g->w8, g->w, b->tasks, L, b->sval, b->smask,   \
                                                    b->sany, b->dist, b->cmask, b->cany, b->fr[0], b->fr[1], b->ctl, \
@@ -1244,25 +1315,29 @@ static void batch_superstep(ipg_graph* g, BatchWorkspace* b, int wkind, uint32_t
 }
 
 // the wide pull's dynamic shared memory for rows of L lines (above the default 48 KB
-// limit for 8 lines); set before the kernel is launched or captured
-template <int V>
-static cudaError_t ring_smem_allow(uint32_t L) {
-    const int bytes = (int)ring_smem_bytes(V, L);
-    cudaError_t e = cudaFuncSetAttribute(batch_pull_ring_kernel<0, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+// limit from 6 lines on); set before the kernel is launched or captured
+template <int L>
+static cudaError_t ring_smem_allow_l() {
+    const int bytes = (int)ring_smem_bytes(L);
+    cudaError_t e = cudaFuncSetAttribute(batch_pull_ring_kernel<0, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_pull_ring_kernel<1, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        e = cudaFuncSetAttribute(batch_pull_ring_kernel<1, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_pull_ring_kernel<2, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        e = cudaFuncSetAttribute(batch_pull_ring_kernel<2, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
 static ipg_status batch_ring_allow(uint32_t lines) {
     cudaError_t e = cudaSuccess;
-    switch (lines_v(lines)) {
-        case 8: e = ring_smem_allow<8>(lines); break;
-        case 4: e = ring_smem_allow<4>(lines); break;
-        case 2: e = ring_smem_allow<2>(lines); break;
-        default: break;
+    switch (lines) {
+        case 1: break;
+        case 2: e = ring_smem_allow_l<2>(); break;
+        case 3: e = ring_smem_allow_l<3>(); break;
+        case 4: e = ring_smem_allow_l<4>(); break;
+        case 5: e = ring_smem_allow_l<5>(); break;
+        case 6: e = ring_smem_allow_l<6>(); break;
+        case 7: e = ring_smem_allow_l<7>(); break;
+        default: e = ring_smem_allow_l<8>(); break;
     }
     return e == cudaSuccess ? IPG_OK : cuda_fail(e, "batched pull shared memory", __FILE__, __LINE__);
 }
