@@ -109,6 +109,7 @@ struct BatchCtl {
     unsigned int live[kMaxLines];            // lanes holding a query, per line
     unsigned int finished[kMaxLines];        // lanes harvested at the end of the last superstep
     unsigned int pending[kMaxLines];         // lanes whose query ended, not harvested yet (list mode)
+    unsigned int final_harvest;              // 1: the last harvest of a session; lanes are not reset
     unsigned int count[kMaxSlots];           // supersteps of each lane's query so far (final once finished)
     unsigned int row[kMaxSlots];             // output row of each lane's query
     // refill from a device list (ipg_sssp_batch): caller ids, nqueries entries
@@ -1002,6 +1003,9 @@ __global__ void batch_step_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __r
         // they wait, so that queries started together are harvested in one pass.
         const bool queued = from_list && ctl->next_query < ctl->nqueries;
         const bool harvest = !from_list || queued || any_live == 0;
+        // with a source list and nothing left to run, the lanes are not reused: the
+        // harvest leaves their values in place and the next session clears them
+        ctl->final_harvest = from_list && !queued && any_live == 0 ? 1u : 0u;
         uint32_t any_harvest = 0;
         for (int i = 0; i < V; ++i) {
             const uint32_t p = ctl->pending[i] | fin_sh[i];
@@ -1038,7 +1042,8 @@ __global__ void batch_step_kernel(BatchCtl* __restrict__ ctl, BatchCounters* __r
 }
 
 // Finished lanes: out[row][v] = dist[inv[v]][line][lane] for every caller id v,
-// and the lane's column back to kInf for its next query.  A thread per caller id
+// and the lane's column back to kInf for its next query (not at a session's final
+// harvest: the next session clears the array in one pass).  A thread per caller id
 // walks the finished lanes of its vertex's row (one row, cached in L1), and the
 // warp's writes of one lane cover 32 consecutive words of its output row.
 template <int V>
@@ -1055,6 +1060,7 @@ __global__ void batch_harvest_kernel(const BatchCtl* __restrict__ ctl, const uin
     __syncthreads();
     uint32_t* __restrict__ out = ctl->out;
     const uint64_t stride = ctl->out_stride;
+    const bool reset = !ctl->final_harvest;
     const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += step) {
         uint32_t* d = dist + (uint64_t)inv[v] * (L * kLanes);
@@ -1063,7 +1069,7 @@ __global__ void batch_harvest_kernel(const BatchCtl* __restrict__ ctl, const uin
             for (uint32_t r = fin_sh[j]; r; r &= r - 1) {
                 const uint32_t b = __ffs(r) - 1;
                 out[(uint64_t)row_sh[j * kLanes + b] * stride + v] = d[j * kLanes + b];
-                d[j * kLanes + b] = kInf;
+                if (reset) d[j * kLanes + b] = kInf;
             }
         }
     }
@@ -1107,6 +1113,8 @@ struct BatchWorkspace {
     size_t list_cap = 0;
     unsigned long long* tasks = nullptr;  // push tasks of the current senders
     bool clean = false;                   // dist/sval all kInf, masks and counters zero
+    bool dist_dirty = false;              // as clean, except dist (left by a final harvest)
+    uint32_t dirty_lines = 0;             // lines of the rows that session used
     ipg_batch_info info{};                // totals of the last ipg_sssp_batch call
     cudaGraphExec_t loop[3][kMaxLines] = {};  // superstep loop, per weight kind and line count
 };
@@ -1388,7 +1396,10 @@ static ipg_status batch_session_begin(ipg_graph* g, BatchWorkspace* b, const Bat
     const size_t n = g->n;
     IPG_TRY(batch_values(g, b, init.lines));
     IPG_TRY(batch_chunks(g, b, st));
-    if (!b->clean) {
+    if (b->clean && b->dist_dirty) {
+        // only the rows the last session used: its lines
+        IPG_CUDA(cudaMemsetAsync(b->dist, 0xFF, sizeof(uint32_t) * kLanes * b->dirty_lines * n, st));
+    } else if (!b->clean) {
         const size_t lines = b->lines;
         IPG_CUDA(cudaMemsetAsync(b->dist, 0xFF, sizeof(uint32_t) * kLanes * lines * n, st));
         IPG_CUDA(cudaMemsetAsync(b->sval, 0xFF, sizeof(uint32_t) * kLanes * lines * n, st));
@@ -1399,6 +1410,7 @@ static ipg_status batch_session_begin(ipg_graph* g, BatchWorkspace* b, const Bat
         IPG_CUDA(cudaMemsetAsync(b->ctr, 0, sizeof(BatchCounters), st));
     }
     b->clean = false;
+    b->dist_dirty = false;
     *b->h_ctl = init;
     IPG_CUDA(cudaMemcpyAsync(b->ctl, b->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, st));
     return IPG_OK;
@@ -1516,7 +1528,9 @@ ipg_status sssp_batch_run(ipg_graph* g, const uint32_t* sources, uint32_t k, uin
         IPG_TRY(batch_launch(g, b, st, "ipg_sssp_batch"));
         if (b->h_ctl->done) break;
     }
-    b->clean = true;  // every lane was harvested
+    b->clean = true;  // every lane was harvested; the last harvest left dist in place
+    b->dist_dirty = true;
+    b->dirty_lines = lines;
     b->info.supersteps = b->h_ctl->supersteps;
     b->info.pull_supersteps = b->h_ctl->pull_supersteps;
     b->info.harvests = b->h_ctl->harvests;
