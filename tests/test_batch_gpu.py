@@ -309,3 +309,21 @@ def test_batch_host_driven_loop_gives_the_same_rows(ipg, k):
         o, cnt, _ = ipg.ipg_sssp(h, int(sources[i]))
         np.testing.assert_array_equal(dist[i], o)
         assert steps[i] == cnt
+
+
+def test_batch_sources_without_out_edges_only(ipg):
+    """Every source without out-edges: no lane runs, each row holds only its source at
+    distance 0, and every count is 1 (superstep 0 alone); also on a graph with no edges."""
+    g = gen.csr_from_edges(6, np.array([0, 1, 2]), np.array([1, 2, 0]), weights=np.array([3, 4, 5], dtype=np.uint32))
+    empty = gen.csr_from_edges(4, np.array([], dtype=np.int64), np.array([], dtype=np.int64))
+    for graph, weights, sources in ((g, g.weights, [3, 4, 5, 5, 3]), (empty, None, [0, 3, 1, 2, 0, 3])):
+        h = ipg.ipg_graph_create(graph.offsets, graph.cols, weights, graph.n, graph.m, True)
+        dist, steps = ipg.ipg_sssp_batch(h, sources)
+        for i, s in enumerate(sources):
+            want = np.full(graph.n, 0xFFFFFFFF, dtype=np.uint32)
+            want[s] = 0
+            np.testing.assert_array_equal(dist[i], want)
+            o = oracle.sssp(graph.n, graph.offsets, graph.cols, weights, int(s))
+            np.testing.assert_array_equal(dist[i], o.values)
+            assert steps[i] == 1 == o.supersteps
+        assert ipg.ipg_sssp_batch_info(h)["supersteps"] == 0
