@@ -617,7 +617,7 @@ def run_other_configs(a):
     out = {}
     jobs = (("pagerank16", lambda b: run_small_config(b, "pagerank16"), dict(steps=20, warmup=3)),
             ("hashmin20", lambda b: run_small_config(b, "hashmin20"), dict(steps=20, warmup=3)),
-            ("batch", run_batch, dict(steps=3, warmup=1)),
+            ("batch", run_batch, dict(steps=5, warmup=2)),
             ("cc_batch", run_cc_batch, dict(steps=5, warmup=2)),
             ("serve", run_serve, dict(requests=6000)),
             ("combiner", run_combiner, dict(steps=5, warmup=2)))
