@@ -518,8 +518,10 @@ void ipg_server_destroy(ipg_server* s);
  *                   percentage of m read a one-bit-per-vertex sender array before
  *                   each gather and gather only from senders; 0 = never (default:
  *                   measured slower on R-MAT 26/28), 100 = every pull superstep.
- *   "batch_chunk"   batched SSSP: in-edges per warp task of the pull form (the
- *                   engine's tile size), a multiple of 32 in [32, 65536].  Default 256.
+ *   "batch_chunk"   batched SSSP: in-edges per warp task of the pull form with one
+ *                   line of 32 lanes (the engine's tile size), a multiple of 32 in
+ *                   [32, 65536].  Default 256.
+ *   "batch_wide_chunk" the same for the pull form with more lines.  Default 512.
  *   "batch_loop"    batched SSSP: 1 = the superstep loop runs on the device inside a
  *                   CUDA graph (one host synchronisation per 1024 supersteps); 0 = the
  *                   host launches every superstep's kernels and reads the loop state

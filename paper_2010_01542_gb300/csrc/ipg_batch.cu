@@ -1099,9 +1099,13 @@ struct BatchWorkspace {
     uint32_t* cany = nullptr;   // [n]: lines with a lowered lane
     uint32_t* fr[2] = {nullptr, nullptr};
     uint32_t* wmax_out = nullptr;  // [n]: largest out-edge weight of each vertex
-    uint32_t* chunk_row = nullptr;
-    uint64_t chunks = 0, chunk_cap = 0;
-    uint32_t chunk = 0;  // in-edges per warp task of the pull form (0: not set up yet)
+    // in-edge chunks of the pull form: [0] for one line (knob batch_chunk), [1] for more
+    // (knob batch_wide_chunk)
+    struct ChunkSet {
+        uint32_t* row = nullptr;  // first row of each chunk
+        uint64_t count = 0, cap = 0;
+        uint32_t size = 0;  // in-edges per chunk (0: not set up yet)
+    } cs[2];
     BatchCounters* ctr = nullptr;
     BatchCtl* ctl = nullptr;
     BatchCtl* h_ctl = nullptr;            // pinned mirror
@@ -1146,7 +1150,8 @@ void batch_free(ipg_graph* g) {
     cudaFree(b->fr[0]);
     cudaFree(b->fr[1]);
     cudaFree(b->wmax_out);
-    cudaFree(b->chunk_row);
+    cudaFree(b->cs[0].row);
+    cudaFree(b->cs[1].row);
     cudaFree(b->ctr);
     cudaFree(b->ctl);
     cudaFree(b->tasks);
@@ -1225,37 +1230,46 @@ static uint32_t batch_lines_for(const ipg_graph* g, const BatchWorkspace* b, uin
     return want > b->lines ? want : (b->lines ? b->lines : 1);
 }
 
-// The in-edge chunks of the pull form (the batched engine's tile size, a tuning knob):
-// their first rows are recomputed, and the loop graphs, which bake in the chunk
-// count, rebuilt, when the size changes.
-static ipg_status batch_chunks(ipg_graph* g, BatchWorkspace* b, cudaStream_t st) {
-    const uint32_t want = (uint32_t)batch_chunk_for(g);
-    if (b->chunk == want) return IPG_OK;
-    batch_drop_loops(b);
+// The in-edge chunks of a pull form (the batched engine's tile sizes, tuning knobs:
+// the one-line and the wide pull measure best at different sizes): their first rows
+// are recomputed, and the loop graphs that use them, which bake in the chunk count,
+// rebuilt, when the size changes.
+static ipg_status batch_chunks(ipg_graph* g, BatchWorkspace* b, uint32_t lines, cudaStream_t st) {
+    const int wide = lines > 1 ? 1 : 0;
+    auto& c = b->cs[wide];
+    const uint32_t want = (uint32_t)(wide ? tuning().batch_wide_chunk : batch_chunk_for(g));
+    if (c.size == want) return IPG_OK;
+    for (auto& per_kind : b->loop)
+        for (int l = 0; l < kMaxLines; ++l)
+            if (per_kind[l] && ((l > 0) == (wide == 1))) {
+                cudaGraphExecDestroy(per_kind[l]);
+                per_kind[l] = nullptr;
+            }
     const uint64_t chunks = (g->m + want - 1) / want;
-    if (chunks > b->chunk_cap) {
-        cudaFree(b->chunk_row);
-        b->chunk_row = nullptr;
-        b->chunk_cap = 0;
-        IPG_CUDA(cudaMalloc(&b->chunk_row, sizeof(uint32_t) * (chunks ? chunks : 1)));
-        b->chunk_cap = chunks;
+    if (chunks > c.cap) {
+        cudaFree(c.row);
+        c.row = nullptr;
+        c.cap = 0;
+        IPG_CUDA(cudaMalloc(&c.row, sizeof(uint32_t) * (chunks ? chunks : 1)));
+        c.cap = chunks;
     }
     if (chunks) {
         chunk_rows_kernel<<<grid_for_warps(chunks / 32 + 1, sm_count_of(g->device)), 256, 0, st>>>(
-            g->csc_off, g->n, g->m, chunks, want, b->chunk_row);
+            g->csc_off, g->n, g->m, chunks, want, c.row);
         IPG_CUDA(cudaGetLastError());
     }
-    b->chunks = chunks;
-    b->chunk = want;
+    c.count = chunks;
+    c.size = want;
     return IPG_OK;
 }
 
 // the wide pull for rows of L lines (2 <= L <= 8)
 template <int K, int L>
 static void ring_launch_l(ipg_graph* g, BatchWorkspace* b, unsigned grid, cudaStream_t st) {
+    const auto& c = b->cs[1];
     batch_pull_ring_kernel<K, L><<<grid, kRingWarps * 32, ring_smem_bytes(L), st>>>(
-        g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row, b->chunks, g->n, g->m, b->sval, b->sany, b->dist,
-        b->cmask, b->cany, b->fr[0], b->fr[1], b->ctl, b->ctr, b->chunk);
+        g->csc_off, g->csc_src, g->csc_w8, g->csc_w, c.row, c.count, g->n, g->m, b->sval, b->sany, b->dist, b->cmask,
+        b->cany, b->fr[0], b->fr[1], b->ctl, b->ctr, c.size);
 }
 
 template <int K>
@@ -1277,13 +1291,14 @@ template <int V>
 static void batch_superstep_lines(ipg_graph* g, BatchWorkspace* b, int wkind, uint32_t L,
                                   cudaGraphConditionalHandle loop, int in_graph, cudaStream_t st) {
     const int sms = sm_count_of(g->device);
-    const unsigned grid = grid_for_warps(b->chunks, sms);
+    const auto& cs = b->cs[L > 1 ? 1 : 0];
+    const unsigned grid = grid_for_warps(cs.count, sms);
     const unsigned fixed = (unsigned)sms * 8;  // frontier passes: persistent, the size is read on the device
 #define IPG_BATCH_PULL(K)                                                                                           \
     if constexpr (V == 1)                                                                                           \
-        batch_pull_kernel<K><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, b->chunk_row,      \
-                                                   b->chunks, g->n, g->m, b->sval, b->smask, b->dist, b->cmask,     \
-                                                   b->fr[0], b->fr[1], b->ctl, b->ctr, b->chunk);                   \
+        batch_pull_kernel<K><<<grid, 256, 0, st>>>(g->csc_off, g->csc_src, g->csc_w8, g->csc_w, cs.row, cs.count,  \
+                                                   g->n, g->m, b->sval, b->smask, b->dist, b->cmask, b->fr[0],      \
+                                                   b->fr[1], b->ctl, b->ctr, cs.size);                              \
     else                                                                                                            \
         batch_ring_launch<K>(g, b, L, 2 * grid, st)
 #define IPG_BATCH_PUSH(K)                                                                                           \
@@ -1395,7 +1410,7 @@ static int weight_kind(const ipg_graph* g) { return g->csc_w8 ? 1 : g->csc_w ? 2
 static ipg_status batch_session_begin(ipg_graph* g, BatchWorkspace* b, const BatchCtl& init, cudaStream_t st) {
     const size_t n = g->n;
     IPG_TRY(batch_values(g, b, init.lines));
-    IPG_TRY(batch_chunks(g, b, st));
+    IPG_TRY(batch_chunks(g, b, init.lines, st));
     if (b->clean && b->dist_dirty) {
         // only the rows the last session used: its lines
         IPG_CUDA(cudaMemsetAsync(b->dist, 0xFF, sizeof(uint32_t) * kLanes * b->dirty_lines * n, st));

@@ -1094,6 +1094,12 @@ ipg_status ipg_set_tuning(const char* name, int64_t value) {
         tuning().batch_loop = value;
         return IPG_OK;
     }
+    if (!strcmp(name, "batch_wide_chunk")) {
+        if (value < 32 || value > 65536 || value % 32)
+            return set_error(IPG_EINVAL, "ipg_set_tuning: batch_wide_chunk must be a multiple of 32 in [32, 65536]");
+        tuning().batch_wide_chunk = value;
+        return IPG_OK;
+    }
     return set_error(IPG_EINVAL, "ipg_set_tuning: unknown knob '%s'", name);
 }
 
@@ -1137,6 +1143,10 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value) {
     }
     if (!strcmp(name, "batch_loop")) {
         *value = tuning().batch_loop;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "batch_wide_chunk")) {
+        *value = tuning().batch_wide_chunk;
         return IPG_OK;
     }
     return set_error(IPG_EINVAL, "ipg_get_tuning: unknown knob '%s'", name);

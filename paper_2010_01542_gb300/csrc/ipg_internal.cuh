@@ -252,6 +252,7 @@ struct Tuning {
     long long pull_filter = 0;   // Hashmin/SSSP pull: check sender bits first below this % of m messages; 0 = never
     long long batch_chunk = 256; // batched SSSP pull: in-edges per warp task (the engine's tile size)
     long long batch_loop = 1;    // batched SSSP: 1 = superstep loop in a CUDA graph, 0 = launched from the host
+    long long batch_wide_chunk = 512;  // batched SSSP pull with more than one line: in-edges per warp task
 };
 Tuning& tuning();
 // the graph's tuned value where it has one, else the process-wide knob

@@ -198,15 +198,19 @@ def test_batch_long_paths_span_several_graph_launches(ipg):
 
 @pytest.mark.parametrize("chunk", [32, 128, 1024, 4096])
 def test_batch_chunk_sizes_give_the_same_rows(ipg, chunk):
-    """The pull form's tile size (in-edges per warp task) changes no row or count."""
+    """The pull forms' tile sizes (in-edges per warp task; batch_chunk with one line of
+    lanes, batch_wide_chunk with more) change no row or count."""
     g = gen.rmat(12, 16, seed=12, weighted=True)
-    sources = np.random.default_rng(12).integers(0, g.n, size=45)
-    old = ipg.ipg_get_tuning("batch_chunk")
+    rng = np.random.default_rng(12)
+    old = ipg.ipg_get_tuning("batch_chunk"), ipg.ipg_get_tuning("batch_wide_chunk")
     try:
         ipg.ipg_set_tuning("batch_chunk", chunk)
-        _check_batch(ipg, g, sources, g.weights)
+        ipg.ipg_set_tuning("batch_wide_chunk", chunk)
+        for k in (20, 45, 150):  # one, two and five lines
+            _check_batch(ipg, g, rng.integers(0, g.n, size=k), g.weights)
     finally:
-        ipg.ipg_set_tuning("batch_chunk", old)
+        ipg.ipg_set_tuning("batch_chunk", old[0])
+        ipg.ipg_set_tuning("batch_wide_chunk", old[1])
 
 
 def _lines_for(g, sources):

@@ -25,6 +25,7 @@ KNOBS = {
     "pull_filter": ([0, 60, 100], [-1, 101]),
     "batch_chunk": ([32, 128, 256, 1024, 65536], [0, 16, 100, 65568]),
     "batch_loop": ([0, 1], [2, -1]),
+    "batch_wide_chunk": ([32, 512, 1024, 65536], [0, 16, 100, 65568]),
 }
 
 
