@@ -38,11 +38,13 @@
 // line j, and with L > 1 sany[u] holds one bit per line that has a sender (the
 // pull form gathers that word per in-edge and loads only the lines it names).
 // With one line, a warp folds each active edge with its 32 lanes, the lanes
-// that do not send from the source skipping their load.  With more, each thread
-// holds V lanes of a row (V = 2, 4 or 8, the next of L: one or two vectors of 8
-// or 16 bytes; lanes past the row's L lines stay unused), and the rows of the
+// that do not send from the source skipping their load.  With more, the pull
+// kernel is instantiated per line count: each thread holds L lanes of a row (a
+// 16-byte vector per 4 lines, one word of each line left), and the rows of the
 // next edges are staged in a per-warp ring in shared memory by cp.async, so that
-// a warp keeps several rows in flight without holding them in registers.
+// a warp keeps several rows in flight without holding them in registers.  The
+// apply and reset passes hold V lanes per thread (V = 2, 4 or 8, the next of L;
+// lanes past the row's L lines stay unused).
 //
 // A sparse superstep runs in push form instead: a task pass cuts the senders'
 // out-edge lists into tasks of kPushChunk edges, and a warp per task sends
@@ -303,58 +305,34 @@ __device__ __forceinline__ void wide_store(uint32_t* __restrict__ row, uint32_t 
         reinterpret_cast<uint4*>(row)[(size_t)k * 32 + t] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Lowered minima of one destination, lines in `pend` (warp-uniform), in two
-// steps so that the atomics' round trip to L2 overlaps the next destination's
-// edges: issue() sends one coalesced row of atomicMin per line and keeps the
-// values they return; finish() (at the next issue, or at the end of the warp's
-// chunk) marks the lanes whose value dropped.  One line: lane b holds run[0] for
-// lane b.  Wide: the thread's words go through the warp's shared buffer `sh` (32 V
-// words) to line order first.
-template <int V>
-struct Flush {
-    uint32_t v = 0, pend = 0;  // destination and its lines (pend == 0: nothing outstanding)
-    uint32_t r[V], old[V];     // lane's minimum and the value its atomicMin found, per line
+// The one-line pull's lowered minima of one destination, in two steps so that
+// the atomic's round trip to L2 overlaps the next destination's edges: issue()
+// sends one coalesced row of atomicMin (lane b holds the minimum for lane b) and
+// keeps the values it returns; finish() (at the next issue, or at the end of the
+// warp's chunk) marks the lanes whose value dropped.  (The wide pull keeps the
+// same two steps inside its kernel.)
+struct Flush1 {
+    uint32_t v = 0, pend = 0;  // destination, and 1 while its atomics are outstanding
+    uint32_t r = kInf, old = kInf;
 
-    __device__ __forceinline__ void finish(uint32_t lane, uint32_t L, uint32_t* __restrict__ cmask,
-                                           uint32_t* __restrict__ cany, uint32_t* __restrict__ next,
+    __device__ __forceinline__ void finish(uint32_t lane, uint32_t* __restrict__ cmask, uint32_t* __restrict__ next,
                                            BatchCounters* __restrict__ ctr) {
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            if (!((pend >> j) & 1u)) continue;
-            const unsigned mask = __ballot_sync(0xFFFFFFFFu, r[j] < old[j]);
-            if (mask && lane == 0) mark_lowered<V>(v, (uint32_t)j, L, mask, cmask, cany, next, ctr);
+        if (pend) {
+            const unsigned mask = __ballot_sync(0xFFFFFFFFu, r < old);
+            if (mask && lane == 0) mark_lowered<1>(v, 0u, 1u, mask, cmask, nullptr, next, ctr);
         }
         pend = 0;
     }
 
-    __device__ __forceinline__ void issue(uint32_t dst, const uint32_t (&run)[V], uint32_t lines, uint32_t lane,
-                                          uint32_t L, uint32_t* __restrict__ sh, uint32_t* __restrict__ dist,
-                                          uint32_t* __restrict__ cmask, uint32_t* __restrict__ cany,
-                                          uint32_t* __restrict__ next, BatchCounters* __restrict__ ctr) {
-        finish(lane, L, cmask, cany, next, ctr);
-        if (V == 1) {
-            r[0] = run[0];
-        } else {
-            using W = Wide<V>;
-#pragma unroll
-            for (int k = 0; k < W::kVec; ++k) {
-                uint32_t w[W::kW];
-#pragma unroll
-                for (int i = 0; i < W::kW; ++i) w[i] = run[k * W::kW + i];
-                wide_store<V>(sh, lane, k, w);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < V; ++j) r[j] = sh[j * kLanes + lane];
-            __syncwarp();  // the buffer is free for the next flush
-        }
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            old[j] = kInf;
-            if (((lines >> j) & 1u) && r[j] != kInf) old[j] = atomicMin(&dist[slot_at(dst, j, lane, L)], r[j]);
-        }
+    __device__ __forceinline__ void issue(uint32_t dst, uint32_t run, uint32_t lane, uint32_t* __restrict__ dist,
+                                          uint32_t* __restrict__ cmask, uint32_t* __restrict__ next,
+                                          BatchCounters* __restrict__ ctr) {
+        finish(lane, cmask, next, ctr);
+        r = run;
+        old = kInf;
+        if (r != kInf) old = atomicMin(&dist[(uint64_t)dst * kLanes + lane], r);
         v = dst;
-        pend = lines;
+        pend = 1;
     }
 };
 
@@ -440,7 +418,7 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
         uint32_t bound = __shfl_sync(0xFFFFFFFFu, win.end_l, 0);  // row end, relative to the chunk (may exceed len)
         uint32_t run[1] = {kInf};
         uint32_t pend = 0;  // some lane folded a message since the last flush (warp-uniform)
-        Flush<1> fl;
+        Flush1 fl;
         uint32_t u_l, w_l, u_1, w_1, u_2, w_2;
         edge_ids<kWeightKind>(csc_src, w8, w32, e_begin, lane, len, u_l, w_l);
         uint32_t a_l = lane < len ? __ldg(smask + u_l) : 0u;
@@ -471,7 +449,7 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
                     if (!one_row) {
                         const uint32_t e = j0 + (uint32_t)jj[q];
                         if (e >= bound) {  // the destination changed (warp-uniform)
-                            if (pend) fl.issue(row, run, pend, lane, 1u, nullptr, dist, cmask, nullptr, next, ctr);
+                            if (pend) fl.issue(row, run[0], lane, dist, cmask, next, ctr);
                             run[0] = kInf;
                             pend = 0;
                             win.seek(csc_off, n, e_begin, e, lane, row, bound);
@@ -484,8 +462,8 @@ __global__ void __launch_bounds__(256) batch_pull_kernel(
             u_l = u_1, w_l = w_1, a_l = a_1;
             u_1 = u_2, w_1 = w_2;
         }
-        if (pend) fl.issue(row, run, pend, lane, 1u, nullptr, dist, cmask, nullptr, next, ctr);
-        fl.finish(lane, 1u, cmask, nullptr, next, ctr);
+        if (pend) fl.issue(row, run[0], lane, dist, cmask, next, ctr);
+        fl.finish(lane, cmask, next, ctr);
     }
 }
 
@@ -529,7 +507,8 @@ template <int L>
 struct RowMap {
     static constexpr int kVec = L / 4;               // vectors: lanes 128 k + 4 t .. + 3 (line 4 k + t / 8)
     static constexpr int kScal = L % 4;              // words: lane 32 (4 kVec + i) + t (line 4 kVec + i)
-    static constexpr int kWords = 4 * kVec + kScal;  // = L
+    static constexpr int kWords = 4 * kVec + kScal;
+    static_assert(kWords == L, "every thread holds exactly L lanes of a row");
     __device__ __forceinline__ static uint32_t vec_off(uint32_t t, int k) { return 128u * k + 4u * t; }
     __device__ __forceinline__ static uint32_t vec_line(uint32_t t, int k) { return 4u * k + t / 8u; }
     __device__ __forceinline__ static uint32_t scal_off(uint32_t t, int i) { return 32u * (4 * kVec + i) + t; }
