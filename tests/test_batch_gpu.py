@@ -331,3 +331,32 @@ def test_batch_sources_without_out_edges_only(ipg):
             np.testing.assert_array_equal(dist[i], o.values)
             assert steps[i] == 1 == o.supersteps
         assert ipg.ipg_sssp_batch_info(h)["supersteps"] == 0
+
+
+@pytest.mark.parametrize("k", [32, 33, 64, 256, 257])
+def test_batch_line_boundaries(ipg, k):
+    """Exactly full lines (32, 64, 256 sources with out-edges), one lane past a full
+    line (33), and one query past the 256 lanes (257, refilled when a lane frees): every
+    row and count equals the standalone run's, and the call uses the lanes it should."""
+    rng = np.random.default_rng(1300 + k)
+    n = 2000
+    src = np.concatenate([np.arange(n), rng.integers(0, n, size=6 * n)])  # every vertex sends
+    dst = rng.integers(0, n, size=src.size)
+    w = rng.integers(1, 256, size=src.size).astype(np.uint32)
+    g = gen.csr_from_edges(n, src, dst, weights=w)
+    sources = rng.choice(n, size=k, replace=False)
+    h = ipg.ipg_graph_create(g.offsets, g.cols, g.weights, g.n, g.m, True)
+    import torch
+
+    d = torch.empty(k * n, dtype=torch.int32, device="cuda")
+    steps = ipg.ipg_sssp_batch_dev(h, sources, d)
+    torch.cuda.synchronize()
+    dist = d.cpu().numpy().view(np.uint32).reshape(k, n)
+    assert ipg.ipg_sssp_batch_info(h)["lanes"] == 32 * min(8, (k + 31) // 32)
+    for i in list(range(0, k, 9)) + [k - 1]:
+        ref, cnt, _ = ipg.ipg_sssp(h, int(sources[i]))
+        np.testing.assert_array_equal(dist[i], ref, err_msg=f"row {i}")
+        assert steps[i] == cnt
+    o = oracle.sssp(n, g.offsets, g.cols, g.weights, int(sources[-1]))
+    np.testing.assert_array_equal(dist[-1], o.values)
+    assert steps[-1] == o.supersteps
