@@ -521,7 +521,9 @@ void ipg_server_destroy(ipg_server* s);
  *   "batch_chunk"   batched SSSP: in-edges per warp task of the pull form with one
  *                   line of 32 lanes (the engine's tile size), a multiple of 32 in
  *                   [32, 65536].  Default 256.
- *   "batch_wide_chunk" the same for the pull form with more lines.  Default 512.
+ *   "batch_wide_chunk" the same for the pull form with more lines, as its largest
+ *                   size: on smaller graphs the engine halves it (not below 128)
+ *                   until each warp of the launch has at least 3 tasks.  Default 512.
  *   "batch_loop"    batched SSSP: 1 = the superstep loop runs on the device inside a
  *                   CUDA graph (one host synchronisation per 1024 supersteps); 0 = the
  *                   host launches every superstep's kernels and reads the loop state

@@ -1216,7 +1216,14 @@ static uint32_t batch_lines_for(const ipg_graph* g, const BatchWorkspace* b, uin
 static ipg_status batch_chunks(ipg_graph* g, BatchWorkspace* b, uint32_t lines, cudaStream_t st) {
     const int wide = lines > 1 ? 1 : 0;
     auto& c = b->cs[wide];
-    const uint32_t want = (uint32_t)(wide ? tuning().batch_wide_chunk : batch_chunk_for(g));
+    uint32_t want = (uint32_t)(wide ? tuning().batch_wide_chunk : batch_chunk_for(g));
+    if (wide) {
+        // the wide pull's warps take every (warps)-th chunk; with fewer than 3 chunks a
+        // warp, the warps holding one chunk more set the superstep's time, so the tile
+        // is halved (down to 128 in-edges) until each warp has 3
+        const uint64_t warps = (uint64_t)2 * grid_for_warps(uint64_t(1) << 40, sm_count_of(g->device)) * kRingWarps;
+        while (want > 128 && (g->m + want - 1) / want < 3 * warps) want >>= 1;
+    }
     if (c.size == want) return IPG_OK;
     for (auto& per_kind : b->loop)
         for (int l = 0; l < kMaxLines; ++l)
