@@ -520,7 +520,10 @@ void ipg_server_destroy(ipg_server* s);
  *                   measured slower on R-MAT 26/28), 100 = every pull superstep.
  *   "batch_chunk"   batched SSSP: in-edges per warp task of the pull form with one
  *                   line of 32 lanes (the engine's tile size), a multiple of 32 in
- *                   [32, 65536].  Default 256.
+ *                   [32, 65536], as its largest size: on smaller graphs the engine
+ *                   halves it (not below 64) until each warp of the launch has at
+ *                   least 3 tasks; a tile the autotuner stored in the graph is used
+ *                   as it is.  Default 256.
  *   "batch_wide_chunk" the same for the pull form with more lines, as its largest
  *                   size: on smaller graphs the engine halves it (not below 128)
  *                   until each warp of the launch has at least 3 tasks.  Default 512.
@@ -550,8 +553,9 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value);
  * order-free; both PageRank engines and every carveout add in one order):
  *   Hashmin, SSSP  pull_divisor in {0, 2, 4, 6, 10, 16, 32};
  *   batched SSSP   (batch_divisor, batch_chunk) in {(6, 256), (0, 256), (2, 256),
- *                  (16, 256), (6, 128), (6, 512), (6, 1024)}: the push/pull switch
- *                  and the tile size of the pull form (in-edges per warp task);
+ *                  (16, 256), (6, 64), (6, 128), (6, 512), (6, 1024)}: the push/pull
+ *                  switch and the tile size of the pull form (in-edges per warp
+ *                  task), which the graph then uses as it is;
  *   PageRank       (pr_engine, pr_carveout) in {(0,-1), (0,60), (1,-1), (1,5)}.
  * Each candidate runs twice (the faster run counts): Hashmin and SSSP to
  * quiescence, batched SSSP on 32 sources (sssp_source and 31 caller ids spread

@@ -1217,12 +1217,16 @@ static ipg_status batch_chunks(ipg_graph* g, BatchWorkspace* b, uint32_t lines, 
     const int wide = lines > 1 ? 1 : 0;
     auto& c = b->cs[wide];
     uint32_t want = (uint32_t)(wide ? tuning().batch_wide_chunk : batch_chunk_for(g));
-    if (wide) {
-        // the wide pull's warps take every (warps)-th chunk; with fewer than 3 chunks a
-        // warp, the warps holding one chunk more set the superstep's time, so the tile
-        // is halved (down to 128 in-edges) until each warp has 3
-        const uint64_t warps = (uint64_t)2 * grid_for_warps(uint64_t(1) << 40, sm_count_of(g->device)) * kRingWarps;
-        while (want > 128 && (g->m + want - 1) / want < 3 * warps) want >>= 1;
+    // The pull's warps take every (warps)-th chunk.  With fewer than 3 chunks a warp, the
+    // warps holding one chunk more set the superstep's time, and with fewer chunks than
+    // warps the launch is short of warps; so the knob's tile is halved, down to a floor
+    // (128 in-edges for the wide pull, 64 for one line), until each warp has 3.  A tile
+    // the autotuner picked for this graph is kept as it is.
+    if (wide || !g->tuned.batch) {
+        const uint64_t cap = grid_for_warps(uint64_t(1) << 40, sm_count_of(g->device));
+        const uint64_t warps = wide ? 2 * cap * kRingWarps : cap * 8;
+        const uint32_t floor = wide ? 128u : 64u;
+        while (want > floor && (g->m + want - 1) / want < 3 * warps) want >>= 1;
     }
     if (c.size == want) return IPG_OK;
     for (auto& per_kind : b->loop)

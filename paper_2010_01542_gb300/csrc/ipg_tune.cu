@@ -17,7 +17,7 @@ constexpr int kSamples = 64;
 const long long kDivisors[] = {0, 2, 4, 6, 10, 16, 32};
 const long long kPrShapes[][2] = {{0, -1}, {0, 60}, {1, -1}, {1, 5}};  // (pr_engine, pr_carveout)
 // batched SSSP: (push/pull divisor, in-edges per warp task of the pull form: the tile size)
-const long long kBatchShapes[][2] = {{6, 256}, {0, 256}, {2, 256}, {16, 256}, {6, 128}, {6, 512}, {6, 1024}};
+const long long kBatchShapes[][2] = {{6, 256}, {0, 256}, {2, 256}, {16, 256}, {6, 64}, {6, 128}, {6, 512}, {6, 1024}};
 
 __global__ void sample_offsets_kernel(const uint64_t* __restrict__ off, uint32_t n, uint64_t* __restrict__ out) {
     const uint32_t i = threadIdx.x;

@@ -65,7 +65,7 @@ def test_autotune_keeps_results(ipg, name, spec):
     rep = ipg.ipg_autotune(h, progs | ipg.IPG_TUNE_FORCE, src)
     assert rep["programs"] == progs and rep["cached"] == 0 and rep["candidates_timed"] > 0
     assert rep["sssp_pull_divisor"] in DIVISORS and rep["sssp_batch_divisor"] in DIVISORS
-    assert rep["sssp_batch_chunk"] in (128, 256, 512, 1024)
+    assert rep["sssp_batch_chunk"] in (64, 128, 256, 512, 1024)
     assert rep["sssp_batch_ms"] > 0
     assert (rep["pr_engine"], rep["pr_carveout"]) in PR_SHAPES
     if hashmin:
