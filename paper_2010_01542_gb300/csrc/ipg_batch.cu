@@ -1225,8 +1225,8 @@ static ipg_status batch_chunks(ipg_graph* g, BatchWorkspace* b, uint32_t lines, 
     if (wide || !g->tuned.batch) {
         const uint64_t cap = grid_for_warps(uint64_t(1) << 40, sm_count_of(g->device));
         const uint64_t warps = wide ? 2 * cap * kRingWarps : cap * 8;
-        const uint32_t floor = wide ? 128u : 64u;
-        while (want > floor && (g->m + want - 1) / want < 3 * warps) want >>= 1;
+        const uint32_t least = wide ? 128u : 64u;
+        while (want > least && (g->m + want - 1) / want < 3 * warps) want >>= 1;
     }
     if (c.size == want) return IPG_OK;
     for (auto& per_kind : b->loop)
