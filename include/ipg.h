@@ -527,6 +527,10 @@ void ipg_server_destroy(ipg_server* s);
  *   "batch_wide_chunk" the same for the pull form with more lines, as its largest
  *                   size: on smaller graphs the engine halves it (not below 128)
  *                   until each warp of the launch has at least 3 tasks.  Default 512.
+ *   "batch_tile_tasks" batched SSSP: the tasks per warp of the launch that the two
+ *                   tile sizes above are halved to reach, in [0, 64]; 0 uses them
+ *                   as they are set.  Halving keeps a tile a multiple of 32.
+ *                   Default 3.
  *   "batch_loop"    batched SSSP: 1 = the superstep loop runs on the device inside a
  *                   CUDA graph (one host synchronisation per 1024 supersteps); 0 = the
  *                   host launches every superstep's kernels and reads the loop state

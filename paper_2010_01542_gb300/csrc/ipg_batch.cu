@@ -1219,14 +1219,16 @@ static ipg_status batch_chunks(ipg_graph* g, BatchWorkspace* b, uint32_t lines, 
     uint32_t want = (uint32_t)(wide ? tuning().batch_wide_chunk : batch_chunk_for(g));
     // The pull's warps take every (warps)-th chunk.  With fewer than 3 chunks a warp, the
     // warps holding one chunk more set the superstep's time, and with fewer chunks than
-    // warps the launch is short of warps; so the knob's tile is halved, down to a floor
-    // (128 in-edges for the wide pull, 64 for one line), until each warp has 3.  A tile
-    // the autotuner picked for this graph is kept as it is.
+    // warps the launch is short of warps; so the knob's tile is halved, while it stays a
+    // multiple of 32 and not below a floor (128 in-edges for the wide pull, 64 for one
+    // line), until each warp has batch_tile_tasks chunks (3; 0 keeps the knob's tile).
+    // A tile the autotuner picked for this graph is kept as it is.
     if (wide || !g->tuned.batch) {
         const uint64_t cap = grid_for_warps(uint64_t(1) << 40, sm_count_of(g->device));
         const uint64_t warps = wide ? 2 * cap * kRingWarps : cap * 8;
+        const uint64_t tasks = (uint64_t)tuning().batch_tile_tasks;
         const uint32_t least = wide ? 128u : 64u;
-        while (want > least && (g->m + want - 1) / want < 3 * warps) want >>= 1;
+        while (want % 64 == 0 && want / 2 >= least && (g->m + want - 1) / want < tasks * warps) want >>= 1;
     }
     if (c.size == want) return IPG_OK;
     for (auto& per_kind : b->loop)

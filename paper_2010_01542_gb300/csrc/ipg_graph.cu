@@ -1100,6 +1100,11 @@ ipg_status ipg_set_tuning(const char* name, int64_t value) {
         tuning().batch_wide_chunk = value;
         return IPG_OK;
     }
+    if (!strcmp(name, "batch_tile_tasks")) {
+        if (value < 0 || value > 64) return set_error(IPG_EINVAL, "ipg_set_tuning: batch_tile_tasks must be in [0, 64]");
+        tuning().batch_tile_tasks = value;
+        return IPG_OK;
+    }
     return set_error(IPG_EINVAL, "ipg_set_tuning: unknown knob '%s'", name);
 }
 
@@ -1147,6 +1152,10 @@ ipg_status ipg_get_tuning(const char* name, int64_t* value) {
     }
     if (!strcmp(name, "batch_wide_chunk")) {
         *value = tuning().batch_wide_chunk;
+        return IPG_OK;
+    }
+    if (!strcmp(name, "batch_tile_tasks")) {
+        *value = tuning().batch_tile_tasks;
         return IPG_OK;
     }
     return set_error(IPG_EINVAL, "ipg_get_tuning: unknown knob '%s'", name);

@@ -253,6 +253,7 @@ struct Tuning {
     long long batch_chunk = 256; // batched SSSP pull: in-edges per warp task (the engine's tile size)
     long long batch_loop = 1;    // batched SSSP: 1 = superstep loop in a CUDA graph, 0 = launched from the host
     long long batch_wide_chunk = 512;  // batched SSSP pull with more than one line: in-edges per warp task
+    long long batch_tile_tasks = 3;    // batched SSSP pull: tasks per warp the tile is halved to reach (0: off)
 };
 Tuning& tuning();
 // the graph's tuned value where it has one, else the process-wide knob

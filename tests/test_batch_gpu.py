@@ -199,18 +199,22 @@ def test_batch_long_paths_span_several_graph_launches(ipg):
 @pytest.mark.parametrize("chunk", [32, 128, 1024, 4096])
 def test_batch_chunk_sizes_give_the_same_rows(ipg, chunk):
     """The pull forms' tile sizes (in-edges per warp task; batch_chunk with one line of
-    lanes, batch_wide_chunk with more) change no row or count."""
+    lanes, batch_wide_chunk with more) change no row or count.  batch_tile_tasks = 0
+    keeps the set sizes on this small graph; 3 (the default) halves them to the floor."""
     g = gen.rmat(12, 16, seed=12, weighted=True)
     rng = np.random.default_rng(12)
-    old = ipg.ipg_get_tuning("batch_chunk"), ipg.ipg_get_tuning("batch_wide_chunk")
+    names = ("batch_chunk", "batch_wide_chunk", "batch_tile_tasks")
+    old = [ipg.ipg_get_tuning(x) for x in names]
     try:
         ipg.ipg_set_tuning("batch_chunk", chunk)
         ipg.ipg_set_tuning("batch_wide_chunk", chunk)
-        for k in (20, 45, 150):  # one, two and five lines
-            _check_batch(ipg, g, rng.integers(0, g.n, size=k), g.weights)
+        for tasks in (0, 3):
+            ipg.ipg_set_tuning("batch_tile_tasks", tasks)
+            for k in (20, 45, 150):  # one, two and five lines
+                _check_batch(ipg, g, rng.integers(0, g.n, size=k), g.weights)
     finally:
-        ipg.ipg_set_tuning("batch_chunk", old[0])
-        ipg.ipg_set_tuning("batch_wide_chunk", old[1])
+        for x, v in zip(names, old):
+            ipg.ipg_set_tuning(x, v)
 
 
 def _lines_for(g, sources):

@@ -26,6 +26,7 @@ KNOBS = {
     "batch_chunk": ([32, 128, 256, 1024, 65536], [0, 16, 100, 65568]),
     "batch_loop": ([0, 1], [2, -1]),
     "batch_wide_chunk": ([32, 512, 1024, 65536], [0, 16, 100, 65568]),
+    "batch_tile_tasks": ([0, 3, 64], [-1, 65]),
 }
 
 
