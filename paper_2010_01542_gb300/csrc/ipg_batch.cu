@@ -10,7 +10,9 @@
 //   refill   free lanes take the next queries (from a device list of sources, or
 //            from seeds the host wrote at a superstep boundary): the source's
 //            value becomes 0 and it joins the current senders;
-//   pull     warps walk contiguous chunks of the in-edge lists (CSC).  Lane b of
+//   pull     warps walk contiguous chunks of the in-edge lists (CSC), each warp
+//            every (warps)-th chunk, with a chunk size halved on smaller graphs
+//            until every warp holds about 3 chunks (see batch_chunks).  Lane b of
 //            line j keeps a running min of sval[u][j][b] + w over the current
 //            destination's edges and flushes it with atomicMin into dist[v][j][b]
 //            when the destination changes (a row split across chunks is finished
